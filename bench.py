@@ -1,0 +1,375 @@
+"""Benchmark: PDIP Newton solves/s at 1e-8 relative residual on the 40^3 pile.
+
+Workload: 40x40x40 polydisperse jittered lattice (radius U[0.4, 0.6], delta =
+0.21, mu = 0.5, dt = 1e-3), padded to 2^20 unknowns.  A step is one PDIP
+iteration of the time step's CCP, continuing the PDIP trajectory from the cold
+start (Sec. 3.3): Schur blocks and rhs, the Newton solve to ||rhs - S dx|| <=
+1e-8 ||rhs|| (FP32 inner PCG + FP64 refinement, Jacobi or QTT preconditioner),
+dlambda, ratio test, backtracking and update.  The L2 is flushed (512 MiB
+write) before every timed step, outside the step's events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precond jacobi|qtt] [--workload pile40p|pile20|pile8]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PDIP Newton solves/s at 1e-8 residual, QTT vs plain PCG; HBM GB/s fraction"
+UNIT = "Newton solves/s"
+WORKLOADS = {
+    "pile40p": "40^3 polydisperse lattice, r~U[0.4,0.6], delta=0.21, mu=0.5, dt=1e-3, 2^20 padded unknowns",
+    "pile20": "20^3 monodisperse lattice, r=0.5, mu=0.5, dt=1e-3, 2^17 padded unknowns",
+    "pile8": "8^3 monodisperse lattice, r=0.5, mu=0.5, dt=1e-3, 2^13 padded unknowns",
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------- our arm
+def solve_bytes(Nc, M, nrow, iters, outer):
+    """Algorithmic bytes of one Newton solve: S-apply per contact/body plus the
+    PCG vector passes, FP32 inner iterations and FP64 outer residuals."""
+    inner = iters * (Nc * 100 + M * 48 + 10 * 4 * nrow)
+    outer_b = (outer + 1) * (Nc * 200 + M * 96 + 5 * 8 * nrow)
+    return inner + outer_b
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1808_02558_gb300 import binding, workload
+    from synth import scene_for
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scene = scene_for(args.workload, seed=1 + rank)
+    ctx = binding.Context()
+    _, con = workload.assemble(ctx, scene)
+    Nc, M, P = con.Nc, con.M, con.P
+    gamma = torch.zeros(P, dtype=torch.float64, device=dev)
+    lam = torch.zeros(2 * Nc, dtype=torch.float64, device=dev)
+    st = ctx.state(gamma, lam)
+    ctx.pdip_init(st, 1.0)
+    mixed = 1 if args.workload == "pile40p" else 0
+    sopts = ctx.solve_opts(tol=1e-8, maxit=200000, mixed=mixed, inner_tol=1e-3 if mixed else 0.0, max_outer=60)
+    opts = ctx.pdip_opts(sopts)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.pdip_step(st, opts, allow=(binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL))
+    torch.cuda.synchronize()
+    barrier(world)
+    step_ms, pcg_ms, iters, outer, relres = [], [], [], [], []
+    launches = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = ctx.pdip_step(st, opts, allow=(binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL))
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            pcg_ms.append(s.solve.ms)
+            iters.append(s.solve.iters)
+            outer.append(s.solve.outer)
+            relres.append(s.solve.rel_res)
+            launches += 4  # pre-step, Jacobi diagonal, persistent PCG, post-step
+        torch.cuda.synchronize()
+        barrier(world)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    solves = sum_over_ranks(float(args.steps), world)
+    value = solves / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (persistent PCG)
+    nrow = 3 * Nc
+    bytes_per = [solve_bytes(Nc, M, nrow, it, ou) for it, ou in zip(iters, outer)]
+    ach = sum(bytes_per) / (sum(pcg_ms) / 1e3) / 1e9
+    peak, src = peaks()
+
+    # end to end through the C ABI with host buffers: H2D scene + state, assemble, step, D2H state
+    host = {k: v.cpu().pin_memory() for k, v in workload.scene_to_device(scene, dev).items()}
+    g_h = gamma.cpu().pin_memory()
+    l_h = lam.cpu().pin_memory()
+    ddev = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    g2 = torch.empty_like(gamma)
+    l2 = torch.empty_like(lam)
+    g_out = torch.empty_like(g_h).pin_memory()
+    l_out = torch.empty_like(l_h).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + g_h.numel() * 8 + l_h.numel() * 8
+    d2h = g_out.numel() * 8 + l_out.numel() * 8
+    ctx2 = binding.Context()
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in host:
+            ddev[k].copy_(host[k], non_blocking=True)
+        g2.copy_(g_h, non_blocking=True)
+        l2.copy_(l_h, non_blocking=True)
+        ctx2.assemble(ddev, scene.floor_z, scene.gravity, scene.dt, scene.delta, scene.mu, 3)
+        st2 = ctx2.state(g2, l2)
+        ctx2.pdip_step(st2, opts, allow=(binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL))
+        g_out.copy_(g2, non_blocking=True)
+        l_out.copy_(l2, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms_max = max_over_ranks(statistics.median(e2e_ms), world)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "contacts": Nc, "bodies": M,
+                   "padded_unknowns": P, "precond": args.precond, "newton_tol": 1e-8,
+                   "solver": "PCG, FP32 inner + FP64 refinement" if mixed else "PCG FP64",
+                   "pdip_iterates": f"iterations {args.warmup}..{args.warmup + args.steps - 1} from the cold start",
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "krylov_iters_per_solve": statistics.mean(iters), "refinements_per_solve": statistics.mean(outer),
+        "max_rel_res": max(relres), "pcg_ms_per_solve": statistics.mean(pcg_ms),
+        "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "hbm", "achieved": ach, "peak": peak,
+                     "unit": "GB/s", "frac": ach / peak, "peak_source": src, "traffic": None},
+        "e2e": {"value": 1e3 / e2e_ms_max * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scene, gamma, lam, statistics.mean(iters) + statistics.mean(outer))
+    ctx2.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------- oracle arm
+def oracle_system(scene, gamma_c=None, lam=None):
+    from oracle import contacts as oc, pdip, qp
+
+    con = oc.detect(scene)
+    D, N, r = qp.qp_data(scene, con)
+    if gamma_c is None:
+        gamma_c, lam = qp.initial_point(con.Nc, scene.mu)
+    f = qp.constraints(gamma_c, scene.mu)
+    t = pdip.NU * 2 * con.Nc / float(-(f @ lam))
+    S = qp.schur_matrix(N, gamma_c, lam, scene.mu)
+    rhs = qp.newton_rhs(N, r, gamma_c, lam, t, scene.mu)
+    return S, rhs
+
+
+def oracle_sample(S, rhs, seconds=12.0):
+    """Run the oracle's Jacobi-PCG for about `seconds`; returns (iters, elapsed)."""
+    from oracle import krylov
+
+    # calibrate: 20 iterations
+    t0 = time.perf_counter()
+    krylov.jacobi_pcg(S, rhs, tol=1e-30, maxit=20)
+    per = (time.perf_counter() - t0) / 20
+    n = max(20, int(seconds / per))
+    t0 = time.perf_counter()
+    _, info = krylov.jacobi_pcg(S, rhs, tol=1e-8, maxit=n)
+    el = time.perf_counter() - t0
+    return info, el
+
+
+def cpu_baseline(scene, gamma=None, lam=None, iters_per_solve=None):
+    from oracle import qp
+
+    g_c = l_c = None
+    if gamma is not None:
+        Nc = lam.numel() // 2
+        g_c = qp.from_padded(gamma.cpu().numpy(), Nc, 3)
+        l_c = lam.cpu().numpy()
+    S, rhs = oracle_system(scene, g_c, l_c)
+    info, el = oracle_sample(S, rhs)
+    per_it = el / max(1, info["iters"])
+    need = info["iters"] if info["converged"] else (iters_per_solve or info["iters"])
+    return {"value": 1.0 / (per_it * need), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FP64 Jacobi-PCG (numpy/scipy, 1 thread) on the same Newton system: {info['iters']} "
+                       f"iterations in {el:.1f} s ({'converged' if info['converged'] else 'capped'}); solves/s = "
+                       f"1/(s per iteration x {need:.0f} iterations per solve"
+                       f"{'' if info['converged'] else ', the GPU count'})")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import scene_for
+
+    scene = scene_for(args.workload, seed=1)
+    S, rhs = oracle_system(scene)
+    times = []
+    its = []
+    for _ in range(args.warmup):
+        oracle_sample(S, rhs, seconds=1.0)
+    for _ in range(args.steps):
+        info, el = oracle_sample(S, rhs, seconds=6.0)
+        times.append(el / max(1, info["iters"]))
+        its.append(info["iters"])
+    per_it = statistics.mean(times)
+    # iterations per solve: a GPU run of the same method on this system needs about
+    # this many (FP64 Jacobi-PCG to 1e-8, first Newton system); the oracle sample is capped
+    need = args.ref_iters
+    value = 1.0 / (per_it * need)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": per_it * need * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "precond": "jacobi",
+                      "newton_tol": 1e-8, "pdip_iterates": "first Newton system of the time step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"oracle FP64 Jacobi-PCG, {statistics.mean(its):.0f} iterations per step "
+                                      f"(~6 s), scaled by {need} iterations per solve"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "qtt"])
+    ap.add_argument("--workload", default="pile40p", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=1000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

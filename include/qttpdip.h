@@ -1,0 +1,229 @@
+/*
+ * qttpdip.h - C ABI of the GB300 library for QTT-accelerated PDIP Newton solves
+ * of the frictional-contact cone complementarity problem (CCP).
+ *
+ * Method: Corona, Gorsich, Jayakumar, Veerapaneni, "Tensor Train accelerated
+ * solvers for nonsmooth rigid body dynamics" (arXiv 1808.02558).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: QP_OK (0) or a negative QP_* code.
+ *    No C++ exception crosses this boundary.  qp_status_string() names a code;
+ *    qp_last_error() returns the message of the last failure on a context.
+ *  - Pointers are DEVICE pointers (memory of the context's device) unless the
+ *    parameter name ends in _host.  Input buffers are borrowed for the call
+ *    only; the caller keeps ownership.  Buffers reported through output structs
+ *    (qp_contacts views, qtt_t handles) are owned by the context and stay
+ *    valid until the next ccp_assemble on that context (views) or until
+ *    qtt_free / qp_destroy (handles).
+ *  - All work is enqueued on the stream given to qp_create.  Functions that
+ *    return statistics or sizes to the host synchronise that stream first.
+ *  - Unknown layout ("padded layout"): contact c owns rows slots*c + {0: n,
+ *    1: t1, 2: t2}; with slots = 4 row 4c+3 is a dummy row.  Rows from
+ *    slots*Nc to P-1 (P = 2^L) are dummy rows too.  Dummy rows of every
+ *    operator are identity rows (Sec. 3.3, uniform tree of 2^L leaves with
+ *    dummy variables); dummy entries of gamma and of right-hand sides are 0.
+ *  - Contacts are ordered by the Morton key of their contact point (Sec. 3.3
+ *    spatial octree hierarchy), ties broken by (body a, body b).
+ */
+#ifndef QTTPDIP_H
+#define QTTPDIP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define QP_OK 0
+#define QP_INVALID_ARG (-1)   /* bad pointer, size or option               */
+#define QP_OOM (-2)           /* device allocation failed                  */
+#define QP_CUDA_ERROR (-3)    /* a CUDA runtime call failed                */
+#define QP_NOT_CONVERGED (-4) /* iteration cap reached before tolerance    */
+#define QP_BREAKDOWN (-5)     /* Krylov breakdown (p'Sp <= 0 or r'z <= 0)  */
+#define QP_LINESEARCH_FAIL (-6) /* PDIP backtracking found no step         */
+#define QP_TIMEOUT (-7)       /* a bounded device-side wait expired        */
+#define QP_NOT_READY (-8)     /* call order violated (e.g. no contacts)    */
+
+typedef enum { QP_F64 = 0, QP_F32 = 1, QP_BF16 = 2 } qp_dtype;
+
+typedef struct qp_ctx* qp_ctx_t;  /* opaque context: device buffers + stream */
+typedef struct qp_qtt* qtt_t;     /* opaque QTT matrix owned by a context    */
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on `device`; `cuda_stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  The context allocates its own device buffers.   */
+int qp_create(qp_ctx_t* out, int device, void* cuda_stream);
+int qp_destroy(qp_ctx_t ctx);
+const char* qp_status_string(int status);
+/* Copy the last error message (NUL-terminated, truncated to len) to buf_host. */
+int qp_last_error(qp_ctx_t ctx, char* buf_host, int len);
+
+/* ---- scene and contact assembly (Sec. 2.2-2.3, 3.3) -------------------- */
+
+typedef struct {
+  int M;                    /* number of spheres                                 */
+  const double* pos;        /* [3*M] SoA: x[0..M), y[M..2M), z[2M..3M)           */
+  const double* vel;        /* [3*M] SoA translational velocity                  */
+  const double* omega;      /* [3*M] SoA angular velocity                        */
+  const double* radius;     /* [M]                                               */
+  const double* inv_mass;   /* [M] 1/m                                           */
+  const double* inv_inertia;/* [M] 1/I (solid spheres: isotropic inertia)        */
+  double floor_z;           /* static floor plane z = floor_z, normal +z         */
+  double gravity[3];        /* body acceleration g (force m g)                   */
+  double dt;                /* time step                                         */
+  double delta;             /* contact envelope: active iff gap Phi <= delta     */
+  double mu;                /* friction coefficient of every contact             */
+  int slots;                /* rows per contact in the padded layout: 3 or 4     */
+} qp_scene;
+
+typedef struct {
+  int M, Nc, L, slots;      /* P = 1 << L padded unknowns                        */
+  long long P;
+  const int* body_a;        /* [Nc] first body; M denotes the static floor       */
+  const int* body_b;        /* [Nc] second body                                  */
+  const double* phi;        /* [Nc] gap function                                 */
+  const double* frame;      /* [9*Nc] SoA: n.x n.y n.z t1.x .. t2.z, each [Nc]   */
+  const double* point;      /* [3*Nc] SoA contact point                          */
+  const double* arm_a;      /* [3*Nc] SoA p - x_a (0 for the floor)              */
+  const double* arm_b;      /* [3*Nc] SoA p - x_b                                */
+  const unsigned long long* key; /* [Nc] Morton key                              */
+  const double* r;          /* [P] padded r = b + D^T M^-1 k (Eq. rdef)          */
+} qp_contacts;
+
+/* Active set A(q, delta) (Sec. 2.2): every sphere pair with gap
+ * Phi = |x_b - x_a| - r_a - r_b <= delta and every sphere with
+ * Phi = z - floor_z - r <= delta.  Builds frames (normal from a to b; t1 =
+ * normalize(n x e), e the axis minimising |n_e|; t2 = n x t1), contact points
+ * p = x_a + n (r_a + Phi/2), arms, Morton keys (21 bits per axis over the
+ * bounding box of the contact points), the ordered list, the body->contact
+ * incidence, and r (Eq. rdef, body force = gravity).  Pair list and order are
+ * bit-exact with an IEEE evaluation in the documented order.  Replaces the
+ * previous contact set of the context (and invalidates earlier views).      */
+int ccp_assemble(qp_ctx_t ctx, const qp_scene* scene, qp_contacts* out);
+
+/* ---- PDIP state and the Newton operator (Sec. 2.4, 3.3) ----------------- */
+
+typedef struct {
+  double* gamma;   /* [P] padded impulses (gn, g1, g2 per contact), dummies 0    */
+  double* lambda;  /* [2*Nc] multipliers: cone constraints, then -gn <= 0       */
+  double t;        /* barrier parameter of the current Newton system (output of
+                      pdip_step; input of newton_solve/newton_apply rhs)        */
+} qp_state;
+
+/* Initial point of Sec. 3.3: gn = gn0 (> 0), gt = 0, lambda_i = -1/f_i.      */
+int pdip_init(qp_ctx_t ctx, qp_state* st, double gn0);
+
+/* y = S x with S = N + blockdiag(H_c(gamma, lambda)) (Schur complement of Eq.
+ * qp_Newton_system, Sec. 3.3) and identity dummy rows; st == NULL gives
+ * y = N x.  N = D^T M^-1 D is applied in factored form (Eq. Ndef): body
+ * gather w = M^-1 D x, then contact projection D^T w, plus the 3x3 block.
+ * dtype QP_F64: x, y double[P]; QP_F32: float[P] (operator data rounded to
+ * FP32).  x and y must not alias.                                           */
+int newton_apply(qp_ctx_t ctx, const qp_state* st, const void* x, void* y, qp_dtype dtype);
+
+/* Newton right-hand side and blocks at (gamma, lambda, t): rhs = -(N gamma + r)
+ * + (1/t) sum_i grad f_i / f_i (padded, dummies 0).                         */
+int newton_rhs(qp_ctx_t ctx, const qp_state* st, double* rhs);
+
+typedef enum { QP_JACOBI_PCG = 0, QP_QTT_PCG = 1 } qp_precond;
+
+typedef struct {
+  qp_precond precond; /* Jacobi (diag S) or the QTT approximate inverse        */
+  qtt_t X;            /* QP_QTT_PCG: preconditioner (approximate S^-1)         */
+  double tol;         /* stop at ||rhs - S dx||_2 <= tol ||rhs||_2             */
+  int maxit;          /* Krylov iteration cap (total inner iterations)         */
+  int mixed;          /* 1: FP32 inner PCG + FP64 outer refinement             */
+  double inner_tol;   /* mixed: relative tolerance of each inner solve         */
+  int max_outer;      /* mixed: refinement cap                                 */
+  qp_dtype core_dtype;/* QTT preconditioner core type (QP_F32 or QP_BF16)      */
+} qp_solve_opts;
+
+typedef struct {
+  int status;         /* QP_OK / QP_NOT_CONVERGED / QP_BREAKDOWN / QP_TIMEOUT */
+  int iters;          /* total Krylov iterations                               */
+  int outer;          /* refinement steps (mixed)                              */
+  double rel_res;     /* true ||rhs - S dx|| / ||rhs|| in FP64                 */
+  double ms;          /* device time of the solve                              */
+} qp_solve_stats;
+
+/* Solve S dx = rhs (S at st) by preconditioned CG, run as one persistent
+ * cooperative kernel (the whole Krylov loop stays on the device).  rhs, dx:
+ * double[P].  stats may be NULL.                                            */
+int newton_solve(qp_ctx_t ctx, const qp_state* st, const double* rhs, double* dx,
+                 const qp_solve_opts* opts, qp_solve_stats* stats);
+
+typedef struct {
+  double nu;          /* t = nu * 2Nc / eta                         (10)       */
+  double alpha;       /* sufficient-decrease factor                 (0.01)     */
+  double beta;        /* backtracking factor                        (0.5)      */
+  double step_frac;   /* fraction of the max dual step              (0.99)     */
+  int max_halvings;   /* backtracking cap                           (60)       */
+  qp_solve_opts solve;/* Newton solve options                                  */
+  int qtt_refresh;    /* 1: compress S and invert it before the solve          */
+  double qtt_eps;     /* TT accuracy of the refresh                            */
+  int qtt_rmax;       /* TT rank cap of the refresh                            */
+} qp_pdip_opts;
+
+typedef struct {
+  int status;
+  double eta;         /* surrogate duality gap at the start of the step        */
+  double t;           /* barrier parameter used                                */
+  double r_dual;      /* ||r_dual|| at the start of the step                   */
+  double r_t;         /* ||r_t|| at the start of the step                      */
+  double s;           /* accepted step length                                  */
+  int halvings;
+  qp_solve_stats solve;
+  double ms_refresh;  /* QTT compress + invert time (device)                   */
+} qp_pdip_stats;
+
+/* One PDIP iteration (Sec. 2.4): eta, t, residuals, Schur blocks and rhs, the
+ * Newton solve, dlambda recovery, ratio test, backtracking on feasibility and
+ * on ||r_t||, update of (gamma, lambda) in place.  Readings of the steps the
+ * paper leaves open follow Boyd and Vandenberghe, Convex Optimization 11.7.  */
+int pdip_step(qp_ctx_t ctx, qp_state* st, const qp_pdip_opts* opts, qp_pdip_stats* stats);
+
+/* Surrogate gap and dual residual norm at st (host scalars).                */
+int pdip_measure(qp_ctx_t ctx, const qp_state* st, double* eta_host, double* r_dual_host);
+
+/* ---- QTT matrices (Sec. 3.1-3.2) --------------------------------------- */
+
+/* Core k (k = 0..d-1) of a QTT matrix is G_k(a, i, j, b), a < r_k, b <
+ * r_{k+1}, stored a-major: index ((a*2 + i)*2 + j)*r_{k+1} + b, i.e. the TT
+ * core (r_k, 4, r_{k+1}) with mode b_k = 2 i_k + j_k.  Row/column bit i_1 is the
+ * most significant bit (Sec. 3.2 tensorisation).                            */
+
+/* Upload cores: ranks_host[d+1] (ranks[0] = ranks[d] = 1), cores_host is the
+ * concatenation of the d cores in the layout above (double).                */
+int qtt_from_host(qp_ctx_t ctx, int d, const int* ranks_host, const double* cores_host, qtt_t* out);
+int qtt_free(qp_ctx_t ctx, qtt_t A);
+int qtt_get_dims(qtt_t A, int* d_host, long long* ncore_values_host);
+int qtt_get_ranks(qtt_t A, int* ranks_host /* [d+1] */);
+int qtt_copy_cores_to_host(qtt_t A, double* cores_host);
+
+/* y = A x, contracting one core at a time (Sec. 3.2 mat-vec, O(r^2 N log N)).
+ * core_dtype: QP_F64, QP_F32 or QP_BF16 (cores rounded to that type; BF16 and
+ * F32 accumulate in FP32).  vec_dtype: QP_F64 (x, y double[2^d]) or QP_F32
+ * (float[2^d]); QP_F64 vectors require QP_F64 cores.                        */
+int qtt_apply(qp_ctx_t ctx, qtt_t A, const void* x, void* y, qp_dtype core_dtype, qp_dtype vec_dtype);
+
+/* TT rounding: right-to-left QR orthogonalisation then left-to-right
+ * truncated SVD in FP64, keeping per split the smallest rank with discarded
+ * norm <= eps ||A||_F / sqrt(d-1), capped at rmax (Sec. 3.1 truncation rule,
+ * Alg. 1 accuracy split).                                                   */
+int qtt_round(qp_ctx_t ctx, qtt_t A, double eps, int rmax, qtt_t* out);
+
+/* QTT compression of S (st != NULL) or of N (st == NULL) in the padded layout:
+ * exact TT-SVD (Alg. 1) of the tensorised sparse matrix, swept right to left
+ * over the nonzero block rows of each level, same truncation rule as above.  */
+int qtt_compress(qp_ctx_t ctx, const qp_state* st, double eps, int rmax, qtt_t* out);
+
+/* Approximate inverse X ~ S^-1 of a QTT matrix by alternating linear-scheme
+ * sweeps with rank adaptation (Sec. 3.2 "TT inversion", two-site variant),
+ * warm-started from `warm` (nullable, must have the same d; Sec. 3.3 inverse
+ * update).  The result is symmetrised, X <- (X + X^T)/2, and rounded.       */
+int qtt_inverse(qp_ctx_t ctx, qtt_t S, double eps, int rmax, int sweeps, qtt_t warm, qtt_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTTPDIP_H */

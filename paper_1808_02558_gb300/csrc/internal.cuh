@@ -1,0 +1,137 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qttpdip.h"
+
+namespace qp {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define QP_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e__ = (call);                                                      \
+    if (e__ != cudaSuccess)                                                        \
+      throw ::qp::Error{QP_CUDA_ERROR, std::string(#call) + ": " + cudaGetErrorString(e__)}; \
+  } while (0)
+
+#define QP_REQUIRE(cond, code, what)                                               \
+  do {                                                                             \
+    if (!(cond)) throw ::qp::Error{(code), std::string(what)};                     \
+  } while (0)
+
+// ---------------------------------------------------------------- buffers
+// Grow-only device buffer; contents are not preserved when it grows.
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+  void* ensure(size_t bytes);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Device-side control block of the persistent kernels.
+struct DevCtl {
+  unsigned int bar_count;  // grid barrier arrivals
+  unsigned int bar_gen;    // grid barrier generation
+  int err;                 // 0 or a QP_* code set by a device-side failure
+  int iters;               // Krylov iterations
+  int outer;               // refinement steps
+  int halvings;
+  double scal[16];         // scalars handed between kernels (eta, t, s, norms, ...)
+};
+
+enum Scal { S_ETA = 0, S_T, S_RDUAL, S_RT, S_S, S_RELRES, S_BNORM, S_SMAX, S_RCENT };
+
+struct QTTCore;
+
+}  // namespace qp
+
+struct qp_qtt {
+  qp_ctx* ctx = nullptr;
+  int d = 0;
+  std::vector<int> ranks;          // d+1
+  std::vector<long long> offset;   // d+1, value offsets of each core
+  long long nvals = 0;
+  double* cores = nullptr;         // FP64 master copy (device)
+  float* cores32 = nullptr;        // FP32 apply copy (device, lazily made)
+  __nv_bfloat16* cores16 = nullptr;// BF16 apply copy (device, lazily made)
+};
+
+struct qp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::string last_error;
+
+  // scene / contact sizes
+  int M = 0, Nc = 0, L = 0, slots = 3;
+  long long P = 0;
+  double mu = 0.5, dt = 1e-3;
+  bool have_contacts = false;
+
+  // contact arrays (FP64 master + FP32 copies for the mixed-precision path)
+  qp::Buf ca, cb, phi, frame, point, arm_a, arm_b, key, r;
+  qp::Buf frame32, arm_a32, arm_b32;
+  // body arrays
+  qp::Buf inv_m, inv_I, inv_m32, inv_I32, bptr, inc;
+  // operator work
+  qp::Buf wbody, wbody32, H, H32, dinv, dinv32;
+  // Krylov / PDIP vectors (P doubles / floats each)
+  qp::Buf v64[8], v32[8];
+  qp::Buf partial;     // per-block partial sums
+  qp::Buf ctl;         // DevCtl
+  qp::Buf scratch[8];  // assembly / QTT scratch
+  qp::DevCtl* ctl_host = nullptr;  // pinned mirror
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace qp {
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Device views of the Schur operator for precision T.
+template <class T>
+struct SysView {
+  int M, Nc, slots;
+  long long P;
+  const int* ca;
+  const int* cb;
+  const T* U;      // [9][Nc]  n, t1, t2
+  const T* ra;     // [3][Nc]
+  const T* rb;     // [3][Nc]
+  const T* inv_m;  // [M]
+  const T* inv_I;  // [M]
+  const int* bptr; // [M+1]
+  const int* inc;  // [2Nc] (contact << 1) | side, side 1 = body b
+  const T* H;      // [6][Nc] packed 3x3 blocks (00 01 02 11 12 22) or null
+  T* w;            // [6][M] body scratch
+};
+
+SysView<double> view64(qp_ctx* c, bool with_H);
+SysView<float> view32(qp_ctx* c, bool with_H);
+
+void set_error(qp_ctx* c, const Error& e);
+void sync(qp_ctx* c);
+
+// kernels launched from several translation units
+void launch_schur_blocks(qp_ctx* c, const double* gamma, const double* lambda);
+void launch_apply64(qp_ctx* c, const double* x, double* y, bool with_H);
+void launch_apply32(qp_ctx* c, const float* x, float* y, bool with_H);
+void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype core_dt, qp_dtype vec_dt);
+void qtt_prepare_copies(qp_ctx* c, qp_qtt* A, qp_dtype core_dt);
+qp_qtt* qtt_alloc(qp_ctx* c, int d, const std::vector<int>& ranks);
+size_t qtt_work_bytes(qp_qtt* A, qp_dtype core_dt);
+
+}  // namespace qp

@@ -1,0 +1,1039 @@
+// Newton-step operator and solvers of the PDIP iteration (Sec. 2.4, 3.3).
+//
+//  * Fused Schur apply y = S x, S = N + blockdiag(H_c), N = D^T M^-1 D (Eq. Ndef)
+//    applied in factored form: a body pass gathers w_b = M_b^-1 sum_c D_cb x_c
+//    over the body's contacts (CSR, fixed order, no atomics), then a contact
+//    pass projects y_c = D_cb^T w_b + D_ca^T w_a + H_c x_c with the 3x3 frame and
+//    block held in registers.
+//  * Schur blocks H_c and the Newton right-hand side (Sec. 3.3 Schur
+//    complement of Eq. qp_Newton_system).
+//  * Preconditioned CG with Jacobi or QTT preconditioner as ONE persistent
+//    cooperative kernel: every phase is a grid-stride loop separated by a
+//    bounded grid barrier; FP64 outer iterative refinement around an inner
+//    PCG in FP64 or FP32.
+//  * PDIP pre-step (gap, t, residual norms, blocks, rhs, Jacobi diagonal) and
+//    post-step (dlambda, ratio test, backtracking, update) as cooperative kernels.
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "internal.cuh"
+#include "qtt_dev.cuh"
+
+namespace qp {
+namespace {
+
+constexpr int NT = 256;               // threads per block of the cooperative kernels
+constexpr int NRED = 8;               // reduction slots per block
+constexpr long long BARRIER_BUDGET = 4000000000LL;  // clock64 ticks (~2 s) per barrier wait
+
+// ------------------------------------------------------------------ barrier
+// Grid barrier with a bounded wait: on expiry it records QP_TIMEOUT in ctl->err
+// and returns false; callers leave the kernel.  Also returns false once any
+// block has recorded an error.
+__device__ bool grid_barrier(DevCtl* ctl, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &ctl->bar_gen;
+    unsigned gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    int good = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > BARRIER_BUDGET) {
+          atomicCAS(&ctl->err, 0, QP_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)&ctl->err) good = 0;
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-reduce n values (sum) and store them as this block's partials.
+template <int N>
+__device__ void block_partials(double (&v)[N], double* partial, int slot0, bool is_min = false) {
+  __shared__ double sm[N][NT / 32];
+  for (int k = 0; k < N; ++k) {
+    double x = is_min ? warp_min(v[k]) : warp_sum(v[k]);
+    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double x = sm[threadIdx.x][0];
+    for (int w = 1; w < NT / 32; ++w) x = is_min ? fmin(x, sm[threadIdx.x][w]) : x + sm[threadIdx.x][w];
+    partial[(size_t)blockIdx.x * NRED + slot0 + threadIdx.x] = x;
+  }
+  __syncthreads();
+}
+
+// Sum (or min) of one partial slot over all blocks, same value in every block.
+__device__ double grid_total(const double* partial, int slot, bool is_min = false) {
+  __shared__ double sm[NT / 32];
+  __shared__ double res;
+  double x = is_min ? 1e300 : 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    double y = *(volatile const double*)&partial[(size_t)b * NRED + slot];
+    x = is_min ? fmin(x, y) : x + y;
+  }
+  x = is_min ? warp_min(x) : warp_sum(x);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = sm[0];
+    for (int w = 1; w < NT / 32; ++w) t = is_min ? fmin(t, sm[w]) : t + sm[w];
+    res = t;
+  }
+  __syncthreads();
+  double out = res;
+  __syncthreads();
+  return out;
+}
+
+// ------------------------------------------------------------------ operator
+template <class T>
+__device__ __forceinline__ void body_gather(const SysView<T>& s, const T* x, int b) {
+  T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
+  const int e = s.bptr[b + 1];
+  const long long n = s.Nc;
+  for (int k = s.bptr[b]; k < e; ++k) {
+    const int code = __ldg(s.inc + k);
+    const int c = code >> 1;
+    const long long row = (long long)s.slots * c;
+    const T x0 = x[row], x1 = x[row + 1], x2 = x[row + 2];
+    const T* U = s.U;
+    T f0 = __ldg(U + c) * x0 + __ldg(U + 3 * n + c) * x1 + __ldg(U + 6 * n + c) * x2;
+    T f1 = __ldg(U + n + c) * x0 + __ldg(U + 4 * n + c) * x1 + __ldg(U + 7 * n + c) * x2;
+    T f2 = __ldg(U + 2 * n + c) * x0 + __ldg(U + 5 * n + c) * x1 + __ldg(U + 8 * n + c) * x2;
+    const T* arm = (code & 1) ? s.rb : s.ra;
+    const T a0 = __ldg(arm + c), a1 = __ldg(arm + n + c), a2 = __ldg(arm + 2 * n + c);
+    if (!(code & 1)) {
+      f0 = -f0;
+      f1 = -f1;
+      f2 = -f2;
+    }
+    F0 += f0;
+    F1 += f1;
+    F2 += f2;
+    Q0 += a1 * f2 - a2 * f1;
+    Q1 += a2 * f0 - a0 * f2;
+    Q2 += a0 * f1 - a1 * f0;
+  }
+  const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+  const long long M = s.M;
+  s.w[b] = im * F0;
+  s.w[M + b] = im * F1;
+  s.w[2 * M + b] = im * F2;
+  s.w[3 * M + b] = iI * Q0;
+  s.w[4 * M + b] = iI * Q1;
+  s.w[5 * M + b] = iI * Q2;
+}
+
+// y_c = U^T [(v_b + w_b x rb) - (v_a + w_a x ra)] + H_c x_c ; returns x_c . y_c
+template <class T>
+__device__ __forceinline__ double contact_apply(const SysView<T>& s, const T* x, T* y, int c) {
+  const long long n = s.Nc, M = s.M;
+  const int a = __ldg(s.ca + c), b = __ldg(s.cb + c);
+  const T* w = s.w;
+  T rb0 = __ldg(s.rb + c), rb1 = __ldg(s.rb + n + c), rb2 = __ldg(s.rb + 2 * n + c);
+  T wb0 = w[3 * M + b], wb1 = w[4 * M + b], wb2 = w[5 * M + b];
+  T d0 = w[b] + (wb1 * rb2 - wb2 * rb1);
+  T d1 = w[M + b] + (wb2 * rb0 - wb0 * rb2);
+  T d2 = w[2 * M + b] + (wb0 * rb1 - wb1 * rb0);
+  if (a < s.M) {
+    T ra0 = __ldg(s.ra + c), ra1 = __ldg(s.ra + n + c), ra2 = __ldg(s.ra + 2 * n + c);
+    T wa0 = w[3 * M + a], wa1 = w[4 * M + a], wa2 = w[5 * M + a];
+    d0 -= w[a] + (wa1 * ra2 - wa2 * ra1);
+    d1 -= w[M + a] + (wa2 * ra0 - wa0 * ra2);
+    d2 -= w[2 * M + a] + (wa0 * ra1 - wa1 * ra0);
+  }
+  const T* U = s.U;
+  const long long row = (long long)s.slots * c;
+  const T x0 = x[row], x1 = x[row + 1], x2 = x[row + 2];
+  T y0 = __ldg(U + c) * d0 + __ldg(U + n + c) * d1 + __ldg(U + 2 * n + c) * d2;
+  T y1 = __ldg(U + 3 * n + c) * d0 + __ldg(U + 4 * n + c) * d1 + __ldg(U + 5 * n + c) * d2;
+  T y2 = __ldg(U + 6 * n + c) * d0 + __ldg(U + 7 * n + c) * d1 + __ldg(U + 8 * n + c) * d2;
+  if (s.H) {
+    const T* H = s.H;
+    T h00 = __ldg(H + c), h01 = __ldg(H + n + c), h02 = __ldg(H + 2 * n + c);
+    T h11 = __ldg(H + 3 * n + c), h12 = __ldg(H + 4 * n + c), h22 = __ldg(H + 5 * n + c);
+    y0 += h00 * x0 + h01 * x1 + h02 * x2;
+    y1 += h01 * x0 + h11 * x1 + h12 * x2;
+    y2 += h02 * x0 + h12 * x1 + h22 * x2;
+  }
+  y[row] = y0;
+  y[row + 1] = y1;
+  y[row + 2] = y2;
+  double dot = (double)x0 * (double)y0 + (double)x1 * (double)y1 + (double)x2 * (double)y2;
+  if (s.slots == 4) {
+    y[row + 3] = x[row + 3];
+    dot += (double)x[row + 3] * (double)x[row + 3];
+  }
+  return dot;
+}
+
+template <class T>
+__global__ void k_body_gather(SysView<T> s, const T* x) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < s.M; b += gridDim.x * blockDim.x) body_gather(s, x, b);
+}
+
+template <class T>
+__global__ void k_contact_apply(SysView<T> s, const T* x, T* y) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.Nc; c += gridDim.x * blockDim.x)
+    contact_apply(s, x, y, c);
+  // dummy tail rows: identity
+  const long long tail0 = (long long)s.slots * s.Nc;
+  for (long long i = tail0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.P;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
+// ------------------------------------------------------------------ PDIP pieces
+struct PdipView {
+  int Nc, slots;
+  double mu;
+  double* gamma;   // [P]
+  double* lambda;  // [2Nc]
+};
+
+// H_c = l_c diag(-mu^2,1,1) + (l_c/(-f_c)) g g^T + (l'_c/gn) e1 e1^T, g = grad f_c
+__device__ __forceinline__ void schur_block(double mu, double gn, double g1, double g2, double lc, double ln,
+                                            double h[6]) {
+  double fc = 0.5 * (g1 * g1 + g2 * g2 - mu * mu * gn * gn);
+  double q0 = -mu * mu * gn, q1 = g1, q2 = g2;
+  double sc = lc / (-fc);
+  h[0] = -mu * mu * lc + sc * q0 * q0 + ln / gn;
+  h[1] = sc * q0 * q1;
+  h[2] = sc * q0 * q2;
+  h[3] = lc + sc * q1 * q1;
+  h[4] = sc * q1 * q2;
+  h[5] = lc + sc * q2 * q2;
+}
+
+__global__ void k_schur_blocks(PdipView v, double* __restrict__ H, float* __restrict__ H32) {
+  const int n = v.Nc;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const long long row = (long long)v.slots * c;
+    double h[6];
+    schur_block(v.mu, v.gamma[row], v.gamma[row + 1], v.gamma[row + 2], v.lambda[c], v.lambda[n + c], h);
+    for (int k = 0; k < 6; ++k) {
+      H[(size_t)k * n + c] = h[k];
+      H32[(size_t)k * n + c] = (float)h[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ PCG kernel
+struct PcgArgs {
+  SysView<double> s64;
+  SysView<float> s32;
+  int nrow;                 // slots * Nc
+  long long P;
+  const double* rhs;        // [P]
+  double* x;                // [P] solution (FP64)
+  double* r64;              // [P] outer residual
+  double* q64;              // [P]
+  // inner vectors, type T (double or float), each [P]
+  void* b;
+  void* e;
+  void* r;
+  void* z;
+  void* p;
+  void* q;
+  const void* dinv;         // Jacobi diagonal inverse (type T)
+  int use_qtt;
+  QttDev qtt;
+  void* qw0;                // QTT work buffers (type T), rmax * P each
+  void* qw1;
+  double tol, inner_tol;
+  int maxit, max_outer;
+  DevCtl* ctl;
+  double* partial;
+};
+
+template <class T>
+__device__ __forceinline__ const SysView<T>& sys_of(const PcgArgs& a);
+template <>
+__device__ __forceinline__ const SysView<double>& sys_of<double>(const PcgArgs& a) { return a.s64; }
+template <>
+__device__ __forceinline__ const SysView<float>& sys_of<float>(const PcgArgs& a) { return a.s32; }
+
+// z = X r through the QTT cores (d grid-synchronised steps).
+template <class T, class TC>
+__device__ bool qtt_precond(const PcgArgs& A, const T* r, T* z) {
+  const QttDev& q = A.qtt;
+  const long long items = A.P >> 1;
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const T* in = r;
+  for (int k = q.d; k >= 1; --k) {
+    T* out = (k == 1) ? z : static_cast<T*>(((q.d - k) & 1) ? A.qw1 : A.qw0);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items; it += gsz)
+      qtt_step_item<T, T, TC>(q, k, in, out, it);
+    if (!grid_barrier(A.ctl, gridDim.x)) return false;
+    in = out;
+  }
+  return true;
+}
+
+// Inner PCG on S_T e = b (x0 = 0) to ||b - S e|| <= tol ||b||.  Returns
+// 0 converged, 1 cap reached, 2 breakdown, -1 barrier failure.
+template <class T, class TC>
+__device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
+  const SysView<T>& s = sys_of<T>(A);
+  T* b = static_cast<T*>(A.b);
+  T* e = static_cast<T*>(A.e);
+  T* r = static_cast<T*>(A.r);
+  T* z = static_cast<T*>(A.z);
+  T* p = static_cast<T*>(A.p);
+  T* q = static_cast<T*>(A.q);
+  const T* dinv = static_cast<const T*>(A.dinv);
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nrow = A.nrow;
+  const unsigned nb = gridDim.x;
+
+  // setup: e = 0, r = b, z = M^-1 r, p = z
+  double acc[2] = {0.0, 0.0};
+  for (long long i = tid; i < nrow; i += gsz) {
+    T bi = b[i];
+    e[i] = 0;
+    r[i] = bi;
+    acc[0] += (double)bi * (double)bi;
+    if (!A.use_qtt) {
+      T zi = dinv[i] * bi;
+      z[i] = zi;
+      p[i] = zi;
+      acc[1] += (double)bi * (double)zi;
+    }
+  }
+  block_partials<2>(acc, A.partial, 0);
+  if (!grid_barrier(A.ctl, nb)) return -1;
+  const double bb = grid_total(A.partial, 0);
+  double rz = grid_total(A.partial, 1);
+  if (bb == 0.0) return 0;
+  if (A.use_qtt) {
+    if (!qtt_precond<T, TC>(A, r, z)) return -1;
+    double a1[1] = {0.0};
+    for (long long i = tid; i < nrow; i += gsz) {
+      T zi = z[i];
+      p[i] = zi;
+      a1[0] += (double)r[i] * (double)zi;
+    }
+    block_partials<1>(a1, A.partial, 1);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    rz = grid_total(A.partial, 1);
+  }
+  const double stop = tol * tol * bb;
+  for (int it = 0; it < maxit; ++it) {
+    if (!(rz > 0.0)) return 2;
+    // q = S p
+    for (int bd = (int)tid; bd < s.M; bd += (int)gsz) body_gather(s, p, bd);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    double a2[1] = {0.0};
+    for (int c = (int)tid; c < s.Nc; c += (int)gsz) a2[0] += contact_apply(s, p, q, c);
+    block_partials<1>(a2, A.partial, 2);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    const double pq = grid_total(A.partial, 2);
+    if (!(pq > 0.0)) return 2;
+    const double alpha = rz / pq;
+    double a3[2] = {0.0, 0.0};
+    for (long long i = tid; i < nrow; i += gsz) {
+      T pi = p[i];
+      e[i] += (T)alpha * pi;
+      T ri = r[i] - (T)alpha * q[i];
+      r[i] = ri;
+      a3[0] += (double)ri * (double)ri;
+      if (!A.use_qtt) {
+        T zi = dinv[i] * ri;
+        z[i] = zi;
+        a3[1] += (double)ri * (double)zi;
+      }
+    }
+    block_partials<2>(a3, A.partial, 3);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    ++iters;
+    const double rr = grid_total(A.partial, 3);
+    double rz_new;
+    if (rr <= stop) return 0;
+    if (A.use_qtt) {
+      if (!qtt_precond<T, TC>(A, r, z)) return -1;
+      double a4[1] = {0.0};
+      for (long long i = tid; i < nrow; i += gsz) a4[0] += (double)r[i] * (double)z[i];
+      block_partials<1>(a4, A.partial, 5);
+      if (!grid_barrier(A.ctl, nb)) return -1;
+      rz_new = grid_total(A.partial, 5);
+    } else {
+      rz_new = grid_total(A.partial, 4);
+    }
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (long long i = tid; i < nrow; i += gsz) p[i] = z[i] + (T)beta * p[i];
+    if (!grid_barrier(A.ctl, nb)) return -1;
+  }
+  return 1;
+}
+
+// FP64 outer refinement: r64 = rhs - S x; inner solve on r64/||r64||; x += ...
+template <class T, class TC>
+__global__ void __launch_bounds__(NT) k_pcg(PcgArgs A) {
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned nb = gridDim.x;
+  const SysView<double>& s64 = A.s64;
+  T* b = static_cast<T*>(A.b);
+  const T* e = static_cast<const T*>(A.e);
+  double a0[1] = {0.0};
+  for (long long i = tid; i < A.P; i += gsz) {
+    A.x[i] = 0.0;
+    if (i < A.nrow) a0[0] += A.rhs[i] * A.rhs[i];
+  }
+  // the QTT preconditioner reads the whole padded vector: keep its tail zero
+  for (long long i = A.nrow + tid; i < A.P; i += gsz) {
+    static_cast<T*>(A.r)[i] = 0;
+    static_cast<T*>(A.z)[i] = 0;
+  }
+  block_partials<1>(a0, A.partial, 6);
+  if (!grid_barrier(A.ctl, nb)) return;
+  const double bnorm = sqrt(grid_total(A.partial, 6));
+  int iters = 0, status = 0, outer = 0;
+  double rel = 0.0;
+  if (bnorm == 0.0) {
+    status = 0;
+  } else {
+    for (outer = 0;; ++outer) {
+      // r64 = rhs - S x
+      double rr[1] = {0.0};
+      if (outer == 0) {
+        for (long long i = tid; i < A.nrow; i += gsz) {
+          A.r64[i] = A.rhs[i];
+          rr[0] += A.rhs[i] * A.rhs[i];
+        }
+      } else {
+        for (int bd = (int)tid; bd < s64.M; bd += (int)gsz) body_gather(s64, A.x, bd);
+        if (!grid_barrier(A.ctl, nb)) return;
+        for (int c = (int)tid; c < s64.Nc; c += (int)gsz) contact_apply(s64, A.x, A.q64, c);
+        if (!grid_barrier(A.ctl, nb)) return;
+        for (long long i = tid; i < A.nrow; i += gsz) {
+          double ri = A.rhs[i] - A.q64[i];
+          A.r64[i] = ri;
+          rr[0] += ri * ri;
+        }
+      }
+      block_partials<1>(rr, A.partial, 7);
+      if (!grid_barrier(A.ctl, nb)) return;
+      const double rn = sqrt(grid_total(A.partial, 7));
+      rel = rn / bnorm;
+      if (rel <= A.tol) {
+        status = 0;
+        break;
+      }
+      if (outer >= A.max_outer || iters >= A.maxit) {
+        status = 1;
+        break;
+      }
+      const double inv = 1.0 / rn;
+      for (long long i = tid; i < A.nrow; i += gsz) b[i] = (T)(A.r64[i] * inv);
+      if (!grid_barrier(A.ctl, nb)) return;
+      int st = inner_pcg<T, TC>(A, A.inner_tol, A.maxit - iters, iters);
+      if (st < 0) return;
+      for (long long i = tid; i < A.nrow; i += gsz) A.x[i] += rn * (double)e[i];
+      if (!grid_barrier(A.ctl, nb)) return;
+      if (st == 2 && iters == 0) {
+        status = 2;
+        break;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.ctl->iters = iters;
+    A.ctl->outer = outer;
+    A.ctl->scal[S_RELRES] = rel;
+    A.ctl->scal[S_BNORM] = bnorm;
+    A.ctl->halvings = status;
+  }
+}
+
+// Jacobi diagonal of S: diag(N) + diag(H); dummy rows 1.
+__global__ void k_diag(SysView<double> s, const double* __restrict__ H, double* __restrict__ d64,
+                       float* __restrict__ d32, long long P) {
+  const long long n = s.Nc;
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += gsz) {
+    long long c = i / s.slots;
+    int u = (int)(i - c * s.slots);
+    double v = 1.0;
+    if (c < n && u < 3) {
+      double U0 = s.U[(3 * u) * n + c], U1 = s.U[(3 * u + 1) * n + c], U2 = s.U[(3 * u + 2) * n + c];
+      int a = s.ca[c], b = s.cb[c];
+      double rb0 = s.rb[c], rb1 = s.rb[n + c], rb2 = s.rb[2 * n + c];
+      double t0 = rb1 * U2 - rb2 * U1, t1 = rb2 * U0 - rb0 * U2, t2 = rb0 * U1 - rb1 * U0;
+      v = s.inv_m[b] + s.inv_I[b] * (t0 * t0 + t1 * t1 + t2 * t2);
+      if (a < s.M) {
+        double ra0 = s.ra[c], ra1 = s.ra[n + c], ra2 = s.ra[2 * n + c];
+        t0 = ra1 * U2 - ra2 * U1;
+        t1 = ra2 * U0 - ra0 * U2;
+        t2 = ra0 * U1 - ra1 * U0;
+        v += s.inv_m[a] + s.inv_I[a] * (t0 * t0 + t1 * t1 + t2 * t2);
+      }
+      if (H) v += H[(u == 0 ? 0 : (u == 1 ? 3 : 5)) * n + c];
+    }
+    d64[i] = 1.0 / v;
+    d32[i] = (float)(1.0 / v);
+  }
+}
+
+// ------------------------------------------------------------------ PDIP kernels
+struct PdipArgs {
+  SysView<double> s;
+  int Nc, slots;
+  long long P;
+  double mu, nu, alpha, beta, step_frac;
+  int max_halvings;
+  double* gamma;
+  double* lambda;
+  const double* r;       // [P]
+  double* Ng;            // [P] N gamma
+  double* rhs;           // [P]
+  double* dg;            // [P] Newton direction
+  double* NDg;           // [P] N dg
+  double* dlam;          // [2Nc]
+  double* H;
+  float* H32;
+  DevCtl* ctl;
+  double* partial;
+};
+
+// gap, t, residual norms, Schur blocks and Newton rhs at (gamma, lambda).
+// mode 0: full pre-step; mode 1: only eta and ||r_dual|| (measurement).
+__global__ void __launch_bounds__(NT) k_pdip_pre(PdipArgs A, int mode) {
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nb = gridDim.x;
+  const int n = A.Nc;
+  SysView<double> s = A.s;
+  s.H = nullptr;
+  // N gamma
+  for (int b = tid; b < s.M; b += (int)gsz) body_gather(s, A.gamma, b);
+  if (!grid_barrier(A.ctl, nb)) return;
+  double acc[1] = {0.0};
+  for (int c = tid; c < n; c += (int)gsz) {
+    contact_apply(s, A.gamma, A.Ng, c);
+    const long long row = (long long)A.slots * c;
+    double gn = A.gamma[row], g1 = A.gamma[row + 1], g2 = A.gamma[row + 2];
+    double fc = 0.5 * (g1 * g1 + g2 * g2 - A.mu * A.mu * gn * gn);
+    acc[0] += -(fc * A.lambda[c] + (-gn) * A.lambda[n + c]);
+  }
+  block_partials<1>(acc, A.partial, 0);
+  if (!grid_barrier(A.ctl, nb)) return;
+  const double eta = grid_total(A.partial, 0);
+  const double t = A.nu * 2.0 * n / eta;
+  double nr[2] = {0.0, 0.0};
+  for (int c = tid; c < n; c += (int)gsz) {
+    const long long row = (long long)A.slots * c;
+    double gn = A.gamma[row], g1 = A.gamma[row + 1], g2 = A.gamma[row + 2];
+    double lc = A.lambda[c], ln = A.lambda[n + c];
+    double mu2 = A.mu * A.mu;
+    double fc = 0.5 * (g1 * g1 + g2 * g2 - mu2 * gn * gn);
+    double q0 = -mu2 * gn;
+    double u0 = A.Ng[row] + A.r[row], u1 = A.Ng[row + 1] + A.r[row + 1], u2 = A.Ng[row + 2] + A.r[row + 2];
+    double rd0 = u0 + lc * q0 - ln, rd1 = u1 + lc * g1, rd2 = u2 + lc * g2;
+    double rc0 = -lc * fc - 1.0 / t, rc1 = -ln * (-gn) - 1.0 / t;
+    nr[0] += rd0 * rd0 + rd1 * rd1 + rd2 * rd2;
+    nr[1] += rc0 * rc0 + rc1 * rc1;
+    if (mode == 0) {
+      double h[6];
+      schur_block(A.mu, gn, g1, g2, lc, ln, h);
+      for (int k = 0; k < 6; ++k) {
+        A.H[(size_t)k * n + c] = h[k];
+        A.H32[(size_t)k * n + c] = (float)h[k];
+      }
+      // rhs = -(N gamma + r) + (1/t) (g/f_c + e1/gn)
+      A.rhs[row] = -u0 + (q0 / fc + 1.0 / gn) / t;
+      A.rhs[row + 1] = -u1 + (g1 / fc) / t;
+      A.rhs[row + 2] = -u2 + (g2 / fc) / t;
+      if (A.slots == 4) A.rhs[row + 3] = 0.0;
+    }
+  }
+  block_partials<2>(nr, A.partial, 1);
+  if (!grid_barrier(A.ctl, nb)) return;
+  const double rd2 = grid_total(A.partial, 1), rc2 = grid_total(A.partial, 2);
+  if (mode == 0) {
+    for (long long i = (long long)A.slots * n + tid; i < A.P; i += gsz) A.rhs[i] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.ctl->scal[S_ETA] = eta;
+    A.ctl->scal[S_T] = t;
+    A.ctl->scal[S_RDUAL] = sqrt(rd2);
+    A.ctl->scal[S_RT] = sqrt(rd2 + rc2);
+  }
+}
+
+// dlambda, ratio test, backtracking (feasibility, then sufficient decrease of
+// ||r_t||), update.  Every block evaluates the same reduced scalars, so all
+// blocks take the same branches.
+__global__ void __launch_bounds__(NT) k_pdip_post(PdipArgs A) {
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nb = gridDim.x;
+  const int n = A.Nc;
+  const double t = A.ctl->scal[S_T];
+  const double rt0 = A.ctl->scal[S_RT];
+  const double mu2 = A.mu * A.mu;
+  SysView<double> s = A.s;
+  s.H = nullptr;
+  // N dg
+  for (int b = tid; b < s.M; b += (int)gsz) body_gather(s, A.dg, b);
+  if (!grid_barrier(A.ctl, nb)) return;
+  double mn[1] = {1e300};
+  for (int c = tid; c < n; c += (int)gsz) {
+    contact_apply(s, A.dg, A.NDg, c);
+    const long long row = (long long)A.slots * c;
+    double gn = A.gamma[row], g1 = A.gamma[row + 1], g2 = A.gamma[row + 2];
+    double d0 = A.dg[row], d1 = A.dg[row + 1], d2 = A.dg[row + 2];
+    double lc = A.lambda[c], ln = A.lambda[n + c];
+    double fc = 0.5 * (g1 * g1 + g2 * g2 - mu2 * gn * gn), fn = -gn;
+    double gdc = -mu2 * gn * d0 + g1 * d1 + g2 * d2, gdn = -d0;
+    double dlc = -lc - 1.0 / (t * fc) - (lc / fc) * gdc;
+    double dln = -ln - 1.0 / (t * fn) - (ln / fn) * gdn;
+    A.dlam[c] = dlc;
+    A.dlam[n + c] = dln;
+    if (dlc < 0.0) mn[0] = fmin(mn[0], -lc / dlc);
+    if (dln < 0.0) mn[0] = fmin(mn[0], -ln / dln);
+  }
+  block_partials<1>(mn, A.partial, 0, true);
+  if (!grid_barrier(A.ctl, nb)) return;
+  double smax = fmin(1.0, grid_total(A.partial, 0, true));
+  double sstep = A.step_frac * smax;
+  int halv = 0;
+  int status = 0;
+  // feasibility: all f(gamma + s dg) < 0
+  for (;;) {
+    double bad[1] = {0.0};
+    for (int c = tid; c < n; c += (int)gsz) {
+      const long long row = (long long)A.slots * c;
+      double gn = A.gamma[row] + sstep * A.dg[row];
+      double g1 = A.gamma[row + 1] + sstep * A.dg[row + 1];
+      double g2 = A.gamma[row + 2] + sstep * A.dg[row + 2];
+      double fc = 0.5 * (g1 * g1 + g2 * g2 - mu2 * gn * gn);
+      if (fc >= 0.0 || -gn >= 0.0) bad[0] += 1.0;
+    }
+    block_partials<1>(bad, A.partial, 1 + (halv & 1));
+    if (!grid_barrier(A.ctl, nb)) return;
+    if (grid_total(A.partial, 1 + (halv & 1)) == 0.0) break;
+    sstep *= A.beta;
+    if (++halv > A.max_halvings) {
+      status = QP_LINESEARCH_FAIL;
+      break;
+    }
+  }
+  // sufficient decrease of ||r_t|| at fixed t
+  while (status == 0) {
+    double nr[1] = {0.0};
+    for (int c = tid; c < n; c += (int)gsz) {
+      const long long row = (long long)A.slots * c;
+      double gn = A.gamma[row] + sstep * A.dg[row];
+      double g1 = A.gamma[row + 1] + sstep * A.dg[row + 1];
+      double g2 = A.gamma[row + 2] + sstep * A.dg[row + 2];
+      double lc = A.lambda[c] + sstep * A.dlam[c];
+      double ln = A.lambda[n + c] + sstep * A.dlam[n + c];
+      double fc = 0.5 * (g1 * g1 + g2 * g2 - mu2 * gn * gn);
+      double u0 = A.Ng[row] + sstep * A.NDg[row] + A.r[row];
+      double u1 = A.Ng[row + 1] + sstep * A.NDg[row + 1] + A.r[row + 1];
+      double u2 = A.Ng[row + 2] + sstep * A.NDg[row + 2] + A.r[row + 2];
+      double rd0 = u0 + lc * (-mu2 * gn) - ln, rd1 = u1 + lc * g1, rd2 = u2 + lc * g2;
+      double rc0 = -lc * fc - 1.0 / t, rc1 = -ln * (-gn) - 1.0 / t;
+      nr[0] += rd0 * rd0 + rd1 * rd1 + rd2 * rd2 + rc0 * rc0 + rc1 * rc1;
+    }
+    block_partials<1>(nr, A.partial, 3 + (halv & 1));
+    if (!grid_barrier(A.ctl, nb)) return;
+    if (sqrt(grid_total(A.partial, 3 + (halv & 1))) <= (1.0 - A.alpha * sstep) * rt0) break;
+    sstep *= A.beta;
+    if (++halv > A.max_halvings) {
+      status = QP_LINESEARCH_FAIL;
+      break;
+    }
+  }
+  if (status == 0) {
+    for (int c = tid; c < n; c += (int)gsz) {
+      const long long row = (long long)A.slots * c;
+      for (int u = 0; u < 3; ++u) A.gamma[row + u] += sstep * A.dg[row + u];
+      A.lambda[c] += sstep * A.dlam[c];
+      A.lambda[n + c] += sstep * A.dlam[n + c];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.ctl->scal[S_S] = sstep;
+    A.ctl->scal[S_SMAX] = smax;
+    A.ctl->halvings = halv;
+    A.ctl->iters = status;
+  }
+}
+
+__global__ void k_pdip_init(int Nc, int slots, long long P, double mu, double gn0, double* gamma, double* lambda) {
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += gsz) {
+    long long c = i / slots;
+    int u = (int)(i - c * slots);
+    gamma[i] = (c < Nc && u == 0) ? gn0 : 0.0;
+    if (i < Nc) {
+      // f_c = -mu^2 gn0^2 / 2, f_{Nc+c} = -gn0; lambda = -1/f
+      lambda[i] = 2.0 / (mu * mu * gn0 * gn0);
+      lambda[Nc + i] = 1.0 / gn0;
+    }
+  }
+}
+
+template <class K>
+int coop_grid(qp_ctx* c, K kernel) {
+  int per_sm = 0;
+  QP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, 0));
+  QP_REQUIRE(per_sm > 0, QP_CUDA_ERROR, "cooperative kernel does not fit on an SM");
+  if (per_sm > 4) per_sm = 4;
+  return per_sm * c->num_sms;
+}
+
+template <class K, class Arg>
+void coop_launch(qp_ctx* c, K kernel, int grid, Arg& a) {
+  void* args[] = {&a};
+  QP_CUDA(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(NT), args, 0, c->stream));
+}
+
+template <class K, class Arg>
+void coop_launch2(qp_ctx* c, K kernel, int grid, Arg& a, int& mode) {
+  void* args[] = {&a, &mode};
+  QP_CUDA(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(NT), args, 0, c->stream));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+void launch_schur_blocks(qp_ctx* c, const double* gamma, const double* lambda) {
+  if (c->Nc == 0) return;
+  PdipView v{c->Nc, c->slots, c->mu, const_cast<double*>(gamma), const_cast<double*>(lambda)};
+  k_schur_blocks<<<ceil_div(c->Nc, 256), 256, 0, c->stream>>>(v, c->H.as<double>(), c->H32.as<float>());
+  QP_CUDA(cudaGetLastError());
+}
+
+void launch_apply64(qp_ctx* c, const double* x, double* y, bool with_H) {
+  SysView<double> s = view64(c, with_H);
+  int g = c->num_sms * 8;
+  if (c->M > 0) k_body_gather<double><<<g, 256, 0, c->stream>>>(s, x);
+  k_contact_apply<double><<<g, 256, 0, c->stream>>>(s, x, y);
+  QP_CUDA(cudaGetLastError());
+}
+
+void launch_apply32(qp_ctx* c, const float* x, float* y, bool with_H) {
+  SysView<float> s = view32(c, with_H);
+  int g = c->num_sms * 8;
+  if (c->M > 0) k_body_gather<float><<<g, 256, 0, c->stream>>>(s, x);
+  k_contact_apply<float><<<g, 256, 0, c->stream>>>(s, x, y);
+  QP_CUDA(cudaGetLastError());
+}
+
+static void reset_ctl(qp_ctx* c) {
+  QP_CUDA(cudaMemsetAsync(c->ctl.p, 0, sizeof(DevCtl), c->stream));
+}
+
+static DevCtl read_ctl(qp_ctx* c) {
+  QP_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+  QP_CUDA(cudaStreamSynchronize(c->stream));
+  return *c->ctl_host;
+}
+
+static PdipArgs pdip_args(qp_ctx* c, const qp_state* st) {
+  PdipArgs A;
+  A.s = view64(c, false);
+  A.Nc = c->Nc;
+  A.slots = c->slots;
+  A.P = c->P;
+  A.mu = c->mu;
+  A.nu = 10.0;
+  A.alpha = 0.01;
+  A.beta = 0.5;
+  A.step_frac = 0.99;
+  A.max_halvings = 60;
+  A.gamma = st->gamma;
+  A.lambda = st->lambda;
+  A.r = c->r.as<double>();
+  const size_t P = (size_t)c->P;
+  A.Ng = static_cast<double*>(c->v64[0].ensure(P * sizeof(double)));
+  A.rhs = static_cast<double*>(c->v64[1].ensure(P * sizeof(double)));
+  A.dg = static_cast<double*>(c->v64[2].ensure(P * sizeof(double)));
+  A.NDg = static_cast<double*>(c->v64[3].ensure(P * sizeof(double)));
+  A.dlam = static_cast<double*>(c->v64[4].ensure(2 * (size_t)(c->Nc > 0 ? c->Nc : 1) * sizeof(double)));
+  A.H = c->H.as<double>();
+  A.H32 = c->H32.as<float>();
+  A.ctl = c->ctl.as<DevCtl>();
+  A.partial = c->partial.as<double>();
+  return A;
+}
+
+static void ensure_partial(qp_ctx* c) {
+  c->partial.ensure((size_t)c->num_sms * 8 * NRED * sizeof(double));
+}
+
+static void check_ready(qp_ctx* c, const qp_state* st) {
+  QP_REQUIRE(c->have_contacts, QP_NOT_READY, "no contacts: call ccp_assemble first");
+  if (st) QP_REQUIRE(st->gamma && st->lambda, QP_INVALID_ARG, "state with null gamma/lambda");
+}
+
+static void pdip_pre(qp_ctx* c, qp_state* st, int mode, const qp_pdip_opts* o) {
+  ensure_partial(c);
+  PdipArgs A = pdip_args(c, st);
+  if (o) {
+    A.nu = o->nu;
+  }
+  int grid = coop_grid(c, k_pdip_pre);
+  reset_ctl(c);
+  coop_launch2(c, k_pdip_pre, grid, A, mode);
+}
+
+// solve S dx = rhs with the current H blocks (already built for st)
+static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o) {
+  ensure_partial(c);
+  QP_REQUIRE(o, QP_INVALID_ARG, "newton_solve: null options");
+  QP_REQUIRE(o->tol > 0 && o->maxit > 0, QP_INVALID_ARG, "newton_solve: tol > 0 and maxit > 0 required");
+  const bool mixed = o->mixed != 0;
+  const bool use_qtt = o->precond == QP_QTT_PCG;
+  QP_REQUIRE(!use_qtt || o->X, QP_INVALID_ARG, "newton_solve: QTT preconditioner requires X");
+  const size_t P = (size_t)c->P;
+  PcgArgs A;
+  A.s64 = view64(c, true);
+  A.s32 = view32(c, true);
+  A.nrow = c->slots * c->Nc;
+  A.P = c->P;
+  A.rhs = rhs;
+  A.x = dx;
+  A.r64 = static_cast<double*>(c->v64[5].ensure(P * sizeof(double)));
+  A.q64 = static_cast<double*>(c->v64[6].ensure(P * sizeof(double)));
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  // inner vectors: for FP64 reuse slots 7 and scratch; keep distinct buffers
+  A.b = (mixed ? c->v32[0] : c->scratch[0]).ensure(P * es);
+  A.e = (mixed ? c->v32[1] : c->scratch[1]).ensure(P * es);
+  A.r = (mixed ? c->v32[2] : c->scratch[2]).ensure(P * es);
+  A.z = (mixed ? c->v32[3] : c->scratch[3]).ensure(P * es);
+  A.p = (mixed ? c->v32[4] : c->scratch[4]).ensure(P * es);
+  A.q = (mixed ? c->v32[5] : c->v64[7]).ensure(P * es);
+  A.dinv = mixed ? (const void*)c->dinv32.p : (const void*)c->dinv.p;
+  A.use_qtt = use_qtt ? 1 : 0;
+  A.qw0 = A.qw1 = nullptr;
+  qp_dtype cdt = QP_F64;
+  if (use_qtt) {
+    qp_qtt* X = o->X;
+    QP_REQUIRE(X->d == c->L, QP_INVALID_ARG, "newton_solve: preconditioner size does not match 2^L");
+    QP_REQUIRE(X->d <= 64, QP_INVALID_ARG, "QTT with more than 64 cores");
+    cdt = mixed ? (o->core_dtype == QP_BF16 ? QP_BF16 : QP_F32) : QP_F64;
+    qtt_prepare_copies(c, X, cdt);
+    A.qtt.d = X->d;
+    int rmax = 1;
+    for (int k = 0; k <= X->d; ++k) {
+      A.qtt.ranks[k] = X->ranks[k];
+      A.qtt.off[k] = X->offset[k];
+      if (X->ranks[k] > rmax) rmax = X->ranks[k];
+    }
+    A.qtt.rmax = rmax;
+    A.qtt.cores = cdt == QP_F64 ? (const void*)X->cores : (cdt == QP_F32 ? (const void*)X->cores32 : (const void*)X->cores16);
+    A.qw0 = (mixed ? c->v32[6] : c->scratch[5]).ensure(P * es * rmax);
+    A.qw1 = (mixed ? c->v32[7] : c->scratch[6]).ensure(P * es * rmax);
+  }
+  A.tol = o->tol;
+  A.inner_tol = mixed ? (o->inner_tol > 0 ? o->inner_tol : 1e-4) : (o->inner_tol > 0 ? o->inner_tol : o->tol);
+  A.maxit = o->maxit;
+  A.max_outer = o->max_outer > 0 ? o->max_outer : (mixed ? 50 : 5);
+  A.ctl = c->ctl.as<DevCtl>();
+  A.partial = c->partial.as<double>();
+
+  // Jacobi diagonal from the current blocks
+  SysView<double> s64 = view64(c, true);
+  k_diag<<<c->num_sms * 4, 256, 0, c->stream>>>(s64, c->H.as<double>(), c->dinv.as<double>(), c->dinv32.as<float>(),
+                                                c->P);
+  QP_CUDA(cudaGetLastError());
+  reset_ctl(c);
+  QP_CUDA(cudaEventRecord(c->ev0, c->stream));
+  if (mixed) {
+    if (cdt == QP_BF16) {
+      auto k = k_pcg<float, __nv_bfloat16>;
+      coop_launch(c, k, coop_grid(c, k), A);
+    } else {
+      auto k = k_pcg<float, float>;
+      coop_launch(c, k, coop_grid(c, k), A);
+    }
+  } else {
+    auto k = k_pcg<double, double>;
+    coop_launch(c, k, coop_grid(c, k), A);
+  }
+  QP_CUDA(cudaEventRecord(c->ev1, c->stream));
+  DevCtl h = read_ctl(c);
+  qp_solve_stats out;
+  float ms = 0;
+  QP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  out.ms = ms;
+  out.iters = h.iters;
+  out.outer = h.outer;
+  out.rel_res = h.scal[S_RELRES];
+  if (h.err) out.status = h.err;
+  else if (h.halvings == 2) out.status = QP_BREAKDOWN;
+  else if (h.halvings == 1) out.status = QP_NOT_CONVERGED;
+  else out.status = QP_OK;
+  return out;
+}
+
+}  // namespace qp
+
+using namespace qp;
+
+#define API_BEGIN(c)            \
+  if (!(c)) return QP_INVALID_ARG; \
+  try {                         \
+    QP_CUDA(cudaSetDevice((c)->device));
+#define API_END(c)               \
+  }                              \
+  catch (const qp::Error& e) {   \
+    qp::set_error((c), e);       \
+    return e.code;               \
+  }                              \
+  return QP_OK;
+
+extern "C" {
+
+int pdip_init(qp_ctx_t c, qp_state* st, double gn0) {
+  API_BEGIN(c)
+  check_ready(c, st);
+  QP_REQUIRE(gn0 > 0, QP_INVALID_ARG, "pdip_init: gn0 must be > 0");
+  k_pdip_init<<<c->num_sms * 4, 256, 0, c->stream>>>(c->Nc, c->slots, c->P, c->mu, gn0, st->gamma, st->lambda);
+  QP_CUDA(cudaGetLastError());
+  st->t = 1.0;
+  API_END(c)
+}
+
+int newton_apply(qp_ctx_t c, const qp_state* st, const void* x, void* y, qp_dtype dt) {
+  API_BEGIN(c)
+  check_ready(c, st);
+  QP_REQUIRE(x && y && x != y, QP_INVALID_ARG, "newton_apply: null or aliased vectors");
+  QP_REQUIRE(dt == QP_F64 || dt == QP_F32, QP_INVALID_ARG, "newton_apply: dtype must be QP_F64 or QP_F32");
+  if (st) launch_schur_blocks(c, st->gamma, st->lambda);
+  if (dt == QP_F64) launch_apply64(c, static_cast<const double*>(x), static_cast<double*>(y), st != nullptr);
+  else launch_apply32(c, static_cast<const float*>(x), static_cast<float*>(y), st != nullptr);
+  API_END(c)
+}
+
+int newton_rhs(qp_ctx_t c, const qp_state* st, double* rhs) {
+  API_BEGIN(c)
+  check_ready(c, st);
+  QP_REQUIRE(st && rhs, QP_INVALID_ARG, "newton_rhs: null state or rhs");
+  pdip_pre(c, const_cast<qp_state*>(st), 0, nullptr);
+  QP_CUDA(cudaMemcpyAsync(rhs, c->v64[1].p, (size_t)c->P * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  DevCtl h = read_ctl(c);
+  QP_REQUIRE(h.err == 0, h.err, "newton_rhs: device wait expired");
+  const_cast<qp_state*>(st)->t = h.scal[S_T];
+  API_END(c)
+}
+
+int newton_solve(qp_ctx_t c, const qp_state* st, const double* rhs, double* dx, const qp_solve_opts* o,
+                 qp_solve_stats* stats) {
+  API_BEGIN(c)
+  check_ready(c, st);
+  QP_REQUIRE(rhs && dx && rhs != dx, QP_INVALID_ARG, "newton_solve: null or aliased vectors");
+  if (st) launch_schur_blocks(c, st->gamma, st->lambda);
+  else QP_CUDA(cudaMemsetAsync(c->H.p, 0, 6 * (size_t)(c->Nc > 0 ? c->Nc : 1) * sizeof(double), c->stream));
+  if (!st) QP_CUDA(cudaMemsetAsync(c->H32.p, 0, 6 * (size_t)(c->Nc > 0 ? c->Nc : 1) * sizeof(float), c->stream));
+  qp_solve_stats s = solve(c, rhs, dx, o);
+  if (stats) *stats = s;
+  if (s.status == QP_TIMEOUT) throw Error{QP_TIMEOUT, "newton_solve: device barrier wait expired"};
+  return s.status;
+  API_END(c)
+}
+
+int pdip_measure(qp_ctx_t c, const qp_state* st, double* eta, double* rdual) {
+  API_BEGIN(c)
+  check_ready(c, st);
+  pdip_pre(c, const_cast<qp_state*>(st), 1, nullptr);
+  DevCtl h = read_ctl(c);
+  QP_REQUIRE(h.err == 0, h.err, "pdip_measure: device wait expired");
+  if (eta) *eta = h.scal[S_ETA];
+  if (rdual) *rdual = h.scal[S_RDUAL];
+  API_END(c)
+}
+
+int pdip_step(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, qp_pdip_stats* stats) {
+  API_BEGIN(c)
+  check_ready(c, st);
+  QP_REQUIRE(o, QP_INVALID_ARG, "pdip_step: null options");
+  qp_pdip_stats out{};
+  pdip_pre(c, st, 0, o);
+  DevCtl h = read_ctl(c);
+  QP_REQUIRE(h.err == 0, h.err, "pdip_step: device wait expired (pre)");
+  out.eta = h.scal[S_ETA];
+  out.t = h.scal[S_T];
+  out.r_dual = h.scal[S_RDUAL];
+  out.r_t = h.scal[S_RT];
+  st->t = out.t;
+  qp_solve_opts so = o->solve;
+  qtt_t X = nullptr;
+  if (o->qtt_refresh && so.precond == QP_QTT_PCG) {
+    cudaEvent_t e0 = c->ev0, e1 = c->ev1;
+    QP_CUDA(cudaEventRecord(e0, c->stream));
+    qtt_t S = nullptr;
+    int rc = qtt_compress(c, st, o->qtt_eps, o->qtt_rmax, &S);
+    if (rc != QP_OK) throw Error{rc, "pdip_step: qtt_compress failed: " + c->last_error};
+    rc = qtt_inverse(c, S, o->qtt_eps, o->qtt_rmax, 4, so.X, &X);
+    qtt_free(c, S);
+    if (rc != QP_OK) throw Error{rc, "pdip_step: qtt_inverse failed: " + c->last_error};
+    QP_CUDA(cudaEventRecord(e1, c->stream));
+    QP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    QP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    out.ms_refresh = ms;
+    so.X = X;
+  }
+  PdipArgs A = pdip_args(c, st);
+  A.nu = o->nu;
+  A.alpha = o->alpha;
+  A.beta = o->beta;
+  A.step_frac = o->step_frac;
+  A.max_halvings = o->max_halvings;
+  // H blocks were built by the pre-step
+  out.solve = solve(c, A.rhs, A.dg, &so);
+  if (X) qtt_free(c, X);
+  if (out.solve.status == QP_TIMEOUT) throw Error{QP_TIMEOUT, "pdip_step: Krylov barrier wait expired"};
+  // keep t in the control block for the post-step
+  reset_ctl(c);
+  QP_CUDA(cudaMemcpyAsync(&c->ctl.as<DevCtl>()->scal[S_T], &out.t, sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  QP_CUDA(cudaMemcpyAsync(&c->ctl.as<DevCtl>()->scal[S_RT], &out.r_t, sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  int grid = coop_grid(c, k_pdip_post);
+  coop_launch(c, k_pdip_post, grid, A);
+  h = read_ctl(c);
+  QP_REQUIRE(h.err == 0, h.err, "pdip_step: device wait expired (post)");
+  out.s = h.scal[S_S];
+  out.halvings = h.halvings;
+  out.status = h.iters != 0 ? h.iters : out.solve.status;
+  if (stats) *stats = out;
+  return out.status;
+  API_END(c)
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+"""GPU parity: fused Schur apply, Newton rhs and the persistent PCG solve (Sec. 2.4, 3.3)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+from gpu_common import Problem, dev, relerr, to_np
+from oracle import pdip, qp
+from paper_1808_02558_gb300 import binding
+from synth import lattice_scene, random_vector, scene_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return binding.Context()
+
+
+@pytest.fixture(scope="module")
+def pile8(ctx):
+    pb = Problem(ctx, scene_for("pile8", 1))
+    pb.iters = {k: pb.oracle_iterates(k) for k in (0, 3)}
+    return pb
+
+
+def interior_point(pb, seed=0):
+    """A strictly feasible (gamma, lambda) with spread values (no PDIP run)."""
+    rng = np.random.default_rng(seed)
+    g = np.zeros(3 * pb.Nc)
+    g[0::3] = rng.uniform(0.5, 20.0, pb.Nc)
+    ang = rng.uniform(0, 2 * np.pi, pb.Nc)
+    rad = rng.uniform(0, 0.9, pb.Nc) * pb.scene.mu * g[0::3]
+    g[1::3], g[2::3] = rad * np.cos(ang), rad * np.sin(ang)
+    lam = rng.uniform(0.01, 5.0, 2 * pb.Nc)
+    return g, lam
+
+
+def check_apply(pb, g, lam, tol64=1e-12, tol32=2e-5):
+    x = random_vector(7, 1, pb.P)
+    xd = dev(x)
+    y = torch.empty_like(xd)
+    # plain N
+    pb.ctx.newton_apply(None, xd, y)
+    want = pb.pad(pb.N @ pb.unpad(x))
+    dummy = np.ones(pb.P, bool)
+    dummy[(pb.slots * np.arange(pb.Nc)[:, None] + np.arange(3)).reshape(-1)] = False
+    want[dummy] = x[dummy]
+    assert relerr(to_np(y), want) <= tol64
+    # Schur S at (g, lam)
+    gd, ld, st = pb.state(g, lam)
+    pb.ctx.newton_apply(st, xd, y)
+    S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+    want = pb.pad(S @ pb.unpad(x))
+    want[dummy] = x[dummy]
+    assert relerr(to_np(y), want) <= tol64
+    x32 = xd.float()
+    y32 = torch.empty_like(x32)
+    pb.ctx.newton_apply(st, x32, y32, binding.QP_F32)
+    assert relerr(to_np(y32).astype(np.float64), want) <= tol32
+
+
+def test_apply_pile8_iterate(pile8):
+    g, lam = pile8.iters[3]
+    check_apply(pile8, g, lam)
+
+
+@pytest.mark.parametrize("slots", [3, 4])
+def test_apply_polydisperse_slots(ctx, slots):
+    pb = Problem(ctx, lattice_scene(6, 3, polydisperse=True), slots)
+    check_apply(pb, *interior_point(pb, 1))
+
+
+def test_apply_full_size_pile40p(ctx):
+    pb = Problem(ctx, scene_for("pile40p", 1))
+    assert pb.P == 1 << 20
+    check_apply(pb, *interior_point(pb, 2))
+
+
+def test_rhs_and_t(pile8):
+    g, lam = pile8.iters[3]
+    gd, ld, st = pile8.state(g, lam)
+    rhs = torch.empty(pile8.P, dtype=torch.float64, device="cuda")
+    pile8.ctx.newton_rhs(st, rhs)
+    f = qp.constraints(g, pile8.scene.mu)
+    t = pdip.NU * 2 * pile8.Nc / float(-(f @ lam))
+    assert abs(st.t - t) <= 1e-12 * t
+    want = pile8.pad(qp.newton_rhs(pile8.N, pile8.r, g, lam, t, pile8.scene.mu))
+    assert relerr(to_np(rhs), want) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [0, 3])
+def test_solve_jacobi_fp64_matches_cholesky(pile8, k):
+    g, lam = pile8.iters[k]
+    gd, ld, st = pile8.state(g, lam)
+    rhs = torch.empty(pile8.P, dtype=torch.float64, device="cuda")
+    pile8.ctx.newton_rhs(st, rhs)
+    dx = torch.empty_like(rhs)
+    stats = pile8.ctx.newton_solve(st, rhs, dx, pile8.ctx.solve_opts(tol=1e-12, maxit=50000), allow=())
+    S = qp.schur_matrix(pile8.N, g, lam, pile8.scene.mu)
+    b = pile8.unpad(to_np(rhs))
+    exact = sla.cho_solve(sla.cho_factor(S.toarray()), b)
+    x = pile8.unpad(to_np(dx))
+    assert np.linalg.norm(b - S @ x) <= 1e-11 * np.linalg.norm(b)
+    assert stats.rel_res <= 1e-12 * 1.0001
+    assert relerr(x, exact) <= 1e-8
+    assert np.all(to_np(dx)[3 * pile8.Nc:] == 0.0)
+
+
+def test_solve_mixed_precision_full_size(ctx):
+    pb = Problem(ctx, scene_for("pile40p", 1))
+    g, lam = interior_point(pb, 3)
+    gd, ld, st = pb.state(g, lam)
+    rhs = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    pb.ctx.newton_rhs(st, rhs)
+    dx = torch.empty_like(rhs)
+    opts = pb.ctx.solve_opts(tol=1e-8, maxit=100000, mixed=1, inner_tol=1e-3, max_outer=60)
+    stats = pb.ctx.newton_solve(st, rhs, dx, opts, allow=())
+    S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+    b = pb.unpad(to_np(rhs))
+    res = np.linalg.norm(b - S @ pb.unpad(to_np(dx))) / np.linalg.norm(b)
+    assert res <= 1.05e-8 and stats.rel_res <= 1e-8
+    assert abs(res - stats.rel_res) <= 1e-9
+
+
+def test_solve_zero_rhs(pile8):
+    g, lam = pile8.iters[0]
+    gd, ld, st = pile8.state(g, lam)
+    rhs = torch.zeros(pile8.P, dtype=torch.float64, device="cuda")
+    dx = torch.full_like(rhs, 7.0)
+    stats = pile8.ctx.newton_solve(st, rhs, dx, pile8.ctx.solve_opts(tol=1e-10), allow=())
+    assert stats.iters == 0 and torch.count_nonzero(dx).item() == 0

@@ -1,0 +1,81 @@
+"""GPU parity: PDIP iterations against the oracle (Sec. 2.4)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import Problem, dev, relerr, to_np
+from oracle import pdip, qp
+from paper_1808_02558_gb300 import binding
+from synth import Scene, lattice_scene, scene_for
+from test_oracle_pdip import closed_form
+from test_oracle_qp import sphere_on_plane
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return binding.Context()
+
+
+def gpu_opts(ctx, tol=1e-12):
+    return ctx.pdip_opts(ctx.solve_opts(tol=tol, maxit=200000))
+
+
+def test_single_step_matches_oracle(ctx):
+    pb = Problem(ctx, scene_for("pile8", 2))
+    g, lam = pb.oracle_iterates(2)
+    g1, l1, info = pdip.pdip_step(pb.N, pb.r, pb.scene.mu, g, lam)
+    gd, ld, st = pb.state(g, lam)
+    stats = ctx.pdip_step(st, gpu_opts(ctx), allow=())
+    assert abs(stats.eta - info.eta) <= 1e-12 * info.eta
+    assert abs(stats.t - info.t) <= 1e-12 * info.t
+    assert abs(stats.r_t - info.r_t_norm) <= 1e-10 * info.r_t_norm
+    assert stats.halvings == info.halvings
+    assert abs(stats.s - info.s) <= 1e-8 * info.s
+    assert relerr(pb.unpad(to_np(gd)), g1) <= 1e-8
+    assert relerr(to_np(ld), l1) <= 1e-8
+
+
+def run_gpu_pdip(ctx, pb, iters, tol_gap=None):
+    g0, l0 = qp.initial_point(pb.Nc, pb.scene.mu)
+    gd, ld, st = pb.state(g0, l0)
+    ctx.pdip_init(st, 1.0)
+    assert relerr(pb.unpad(to_np(gd)), g0) == 0.0 and relerr(to_np(ld), l0) <= 1e-15
+    opts = gpu_opts(ctx)
+    for _ in range(iters):
+        if tol_gap is not None:
+            eta, _ = ctx.pdip_measure(st)
+            if eta <= tol_gap:
+                break
+        ctx.pdip_step(st, opts, allow=())
+    return pb.unpad(to_np(gd)), to_np(ld)
+
+
+def test_trajectory_pile8(ctx):
+    pb = Problem(ctx, scene_for("pile8", 1))
+    K = 6
+    g, lam = pb.oracle_iterates(K)
+    gg, ll = run_gpu_pdip(ctx, pb, K)
+    assert relerr(gg, g) <= 1e-6 and relerr(ll, lam) <= 1e-6
+
+
+@pytest.mark.parametrize("vel,kind", [((0.01, 0.0, -0.5), "stick"), ((2.0, 0.5, -0.1), "slip")])
+def test_sphere_on_plane_final_impulses(ctx, vel, kind):
+    s = sphere_on_plane(vel)
+    pb = Problem(ctx, s)
+    want, k = closed_form(s.mass[0], s.mu, pb.r[0], pb.r[1:3])
+    assert k == kind
+    gg, _ = run_gpu_pdip(ctx, pb, 200, tol_gap=1e-12)
+    assert np.allclose(gg, want, rtol=0, atol=1e-6 * max(1.0, np.abs(want).max()) * s.mass[0])
+
+
+def test_small_lattice_final_impulses(ctx):
+    s = lattice_scene(2, 1)
+    pb = Problem(ctx, s)
+    res = pdip.pdip_solve(pb.N, pb.r, s.mu, tol_gap=1e-8, tol_dual=1e-6, maxit=200)
+    gg, _ = run_gpu_pdip(ctx, pb, res.iters)
+    assert relerr(gg, res.gamma) <= 1e-6
+    assert relerr(pb.D @ gg, pb.D @ res.gamma) <= 1e-6
