@@ -445,7 +445,8 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   QP_CUDA(cudaStreamSynchronize(st));
 
   const int slots = s->slots;
-  long long rows = (long long)slots * (Nc > 0 ? Nc : 1);
+  long long rows = (long long)slots * Nc;
+  if (rows < 1) rows = 1;
   int L = 1;
   while ((1LL << L) < rows) ++L;
   const long long P = 1LL << L;
@@ -463,7 +464,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   char* raw = static_cast<char*>(c->scratch[6].ensure(n * (2 * sizeof(int) + 7 * sizeof(double)) + 256));
   int* wa = reinterpret_cast<int*>(raw);
   int* wb = wa + n;
-  double* phi_raw = reinterpret_cast<double*>(wb + n + (n & 1));
+  double* phi_raw = reinterpret_cast<double*>(wb + n);  // 2n ints: 8-byte aligned
   double* nrm_raw = phi_raw + n;
   double* pt_raw = nrm_raw + 3 * n;
   char* keys = static_cast<char*>(c->scratch[7].ensure(n * (4 * sizeof(unsigned long long) + 4 * sizeof(int)) + 256));

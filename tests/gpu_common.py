@@ -18,9 +18,11 @@ class Problem:
     """A scene assembled by both the oracle and the library."""
 
     def __init__(self, ctx, scene, slots=3):
+        # a context holds one contact set: every problem gets its own context
         self.scene = scene
         self.slots = slots
-        self.ctx = ctx
+        self.ctx = binding.Context()
+        ctx = self.ctx
         self.dev, self.con = workload.assemble(ctx, scene, slots)
         self.oc = oc.detect(scene)
         self.D, self.N, self.r = qp.qp_data(scene, self.oc)

@@ -29,7 +29,7 @@ def test_single_step_matches_oracle(ctx):
     g, lam = pb.oracle_iterates(2)
     g1, l1, info = pdip.pdip_step(pb.N, pb.r, pb.scene.mu, g, lam)
     gd, ld, st = pb.state(g, lam)
-    stats = ctx.pdip_step(st, gpu_opts(ctx), allow=())
+    stats = pb.ctx.pdip_step(st, gpu_opts(pb.ctx), allow=())
     assert abs(stats.eta - info.eta) <= 1e-12 * info.eta
     assert abs(stats.t - info.t) <= 1e-12 * info.t
     assert abs(stats.r_t - info.r_t_norm) <= 1e-10 * info.r_t_norm
@@ -40,6 +40,7 @@ def test_single_step_matches_oracle(ctx):
 
 
 def run_gpu_pdip(ctx, pb, iters, tol_gap=None):
+    ctx = pb.ctx
     g0, l0 = qp.initial_point(pb.Nc, pb.scene.mu)
     gd, ld, st = pb.state(g0, l0)
     ctx.pdip_init(st, 1.0)
