@@ -223,6 +223,31 @@ int qtt_compress(qp_ctx_t ctx, const qp_state* st, double eps, int rmax, qtt_t* 
  * update).  The result is symmetrised, X <- (X + X^T)/2, and rounded.       */
 int qtt_inverse(qp_ctx_t ctx, qtt_t S, double eps, int rmax, int sweeps, qtt_t warm, qtt_t* out);
 
+/* ---- allocation-free QTT mat-vec ---------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc, for example code running inside a host application
+ * that owns the device memory pool, or that must keep a fixed device footprint.
+ * It needs no context and allocates nothing: the caller passes the cores, x
+ * and y, and the two intermediate buffers come from a static device array of
+ * 2 * QTT_NOALLOC_MAX_VALUES floats (32 MiB) that every GPU which loads this
+ * library holds until the process exits.
+ *
+ * y = A x as qtt_apply(..., QP_F32, QP_F32) computes it: d = number of cores,
+ * ranks_host[d+1] (host, ranks[0] = ranks[d] = 1), cores = device float32
+ * values in the core layout above, x and y device float32 [2^d], no aliasing;
+ * work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy stream) of the
+ * current device.  Returns QP_INVALID_ARG when max_k(r_k) * 2^d exceeds
+ * QTT_NOALLOC_MAX_VALUES (e.g. d = 17 allows ranks up to 32, d = 20 up to 4),
+ * or for bad pointers/ranks.
+ * The first call on a device looks up the device address of the static array
+ * (once per device); make that first call before any stream capture.  Every
+ * call shares the same array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it; serialise them.                  */
+#define QTT_NOALLOC_MAX_VALUES (1LL << 22)
+int qtt_apply_f32_noalloc(int d, const int* ranks_host, const float* cores, const float* x, float* y,
+                          void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,11 +20,12 @@ QP_OK, QP_INVALID_ARG, QP_OOM, QP_CUDA_ERROR = 0, -1, -2, -3
 QP_NOT_CONVERGED, QP_BREAKDOWN, QP_LINESEARCH_FAIL, QP_TIMEOUT, QP_NOT_READY = -4, -5, -6, -7, -8
 QP_F64, QP_F32, QP_BF16 = 0, 1, 2
 QP_JACOBI_PCG, QP_QTT_PCG = 0, 1
+QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
            "newton_apply", "newton_rhs", "newton_solve", "pdip_step", "pdip_measure", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
-           "qtt_compress", "qtt_inverse"]
+           "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
 
 
 class Scene(C.Structure):
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH):
         "qtt_round": (i, [vp, vp, d, i, C.POINTER(vp)]),
         "qtt_compress": (i, [vp, C.POINTER(State), d, i, C.POINTER(vp)]),
         "qtt_inverse": (i, [vp, vp, d, i, i, vp, C.POINTER(vp)]),
+        "qtt_apply_f32_noalloc": (i, [i, C.POINTER(i), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -107,6 +109,18 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def qtt_apply_f32_noalloc(ranks: list, cores, x, y, stream=None) -> int:
+    """Context-free, allocation-free y = A x (float32 cores and vectors); returns the status."""
+    import torch
+
+    lib = load()
+    d = len(ranks) - 1
+    r = (C.c_int * (d + 1))(*ranks)
+    s = torch.cuda.current_stream() if stream is None else stream
+    return lib.qtt_apply_f32_noalloc(d, r, C.c_void_p(cores.data_ptr()), C.c_void_p(x.data_ptr()),
+                                     C.c_void_p(y.data_ptr()), C.c_void_p(s.cuda_stream))
 
 
 class QPError(RuntimeError):
