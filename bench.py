@@ -170,8 +170,11 @@ def run_ours(args):
     st = ctx.state(gamma, lam)
     ctx.pdip_init(st, 1.0)
     mixed = 1 if args.workload == "pile40p" else 0
-    sopts = ctx.solve_opts(tol=1e-8, maxit=200000, mixed=mixed, inner_tol=1e-3 if mixed else 0.0, max_outer=60)
-    opts = ctx.pdip_opts(sopts)
+    qtt = args.precond == "qtt"
+    sopts = ctx.solve_opts(binding.QP_QTT_PCG if qtt else binding.QP_JACOBI_PCG, None, tol=1e-8, maxit=200000,
+                           mixed=mixed, inner_tol=1e-3 if mixed else 0.0, max_outer=60,
+                           core_dtype=binding.QP_BF16 if mixed else binding.QP_F32)
+    opts = ctx.pdip_opts(sopts, qtt_refresh=1 if qtt else 0, qtt_eps=args.qtt_eps, qtt_rmax=args.qtt_rmax)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -179,7 +182,7 @@ def run_ours(args):
         ctx.pdip_step(st, opts, allow=(binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL))
     torch.cuda.synchronize()
     barrier(world)
-    step_ms, pcg_ms, iters, outer, relres = [], [], [], [], []
+    step_ms, pcg_ms, iters, outer, relres, refresh_ms = [], [], [], [], [], []
     launches = 0
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -197,7 +200,10 @@ def run_ours(args):
             iters.append(s.solve.iters)
             outer.append(s.solve.outer)
             relres.append(s.solve.rel_res)
+            refresh_ms.append(s.ms_refresh)
             launches += 4  # pre-step, Jacobi diagonal, persistent PCG, post-step
+            if qtt:
+                launches += 2 * con.L + 40  # compression levels, inverse, rounding (approximate)
         torch.cuda.synchronize()
         barrier(world)
     total_ms = max_over_ranks(sum(step_ms), world)
@@ -251,6 +257,7 @@ def run_ours(args):
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
         "krylov_iters_per_solve": statistics.mean(iters), "refinements_per_solve": statistics.mean(outer),
         "max_rel_res": max(relres), "pcg_ms_per_solve": statistics.mean(pcg_ms),
+        "qtt_refresh_ms_per_step": statistics.mean(refresh_ms) if qtt else None,
         "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "hbm", "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak, "peak_source": src, "traffic": None},
         "e2e": {"value": 1e3 / e2e_ms_max * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -362,6 +369,8 @@ def main():
     ap.add_argument("--workload", default="pile40p", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000)
+    ap.add_argument("--qtt-eps", type=float, default=1e-2)
+    ap.add_argument("--qtt-rmax", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -159,7 +159,9 @@ typedef struct {
   double step_frac;   /* fraction of the max dual step              (0.99)     */
   int max_halvings;   /* backtracking cap                           (60)       */
   qp_solve_opts solve;/* Newton solve options                                  */
-  int qtt_refresh;    /* 1: compress S and invert it before the solve          */
+  int qtt_refresh;    /* 1: compress S and invert it before the solve; the new
+                         inverse is kept by the context and warm-starts the
+                         next refresh (solve.X, when set, is the warm start)   */
   double qtt_eps;     /* TT accuracy of the refresh                            */
   int qtt_rmax;       /* TT rank cap of the refresh                            */
 } qp_pdip_opts;
@@ -214,7 +216,10 @@ int qtt_round(qp_ctx_t ctx, qtt_t A, double eps, int rmax, qtt_t* out);
 
 /* QTT compression of S (st != NULL) or of N (st == NULL) in the padded layout:
  * exact TT-SVD (Alg. 1) of the tensorised sparse matrix, swept right to left
- * over the nonzero block rows of each level, same truncation rule as above.  */
+ * over the nonzero block rows of each level, same truncation rule as above.
+ * Ranks are capped at min(rmax, 128).  The SVDs go through FP64 Gram matrices,
+ * which resolve singular values down to about 1e-8 of the largest one, so eps
+ * below about 1e-7 does not reduce the error further (same for qtt_round).  */
 int qtt_compress(qp_ctx_t ctx, const qp_state* st, double eps, int rmax, qtt_t* out);
 
 /* Approximate inverse X ~ S^-1 of a QTT matrix by alternating linear-scheme

@@ -256,8 +256,8 @@ __global__ void k_gather(int n, int M, const int* __restrict__ perm2, const int*
                          const double* __restrict__ nrm_raw, const double* __restrict__ pt_raw,
                          const double* __restrict__ pos, int* __restrict__ ca, int* __restrict__ cb,
                          double* __restrict__ phi, double* __restrict__ frame, double* __restrict__ point,
-                         double* __restrict__ arm_a, double* __restrict__ arm_b, float* __restrict__ frame32,
-                         float* __restrict__ arm_a32, float* __restrict__ arm_b32) {
+                         double* __restrict__ arm_a, double* __restrict__ arm_b, double* __restrict__ rec64,
+                         float* __restrict__ rec32) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   int j = perm1[perm2[c]];
@@ -286,10 +286,15 @@ __global__ void k_gather(int n, int M, const int* __restrict__ perm2, const int*
   double t2y = dsub(dmul(nz, t1x), dmul(nx, t1z));
   double t2z = dsub(dmul(nx, t1y), dmul(ny, t1x));
   double F[9] = {nx, ny, nz, t1x, t1y, t1z, t2x, t2y, t2z};
+  double* R = rec64 + (size_t)c * 16;
+  float* R32 = rec32 + (size_t)c * 16;
   for (int k = 0; k < 9; ++k) {
     frame[(size_t)k * n + c] = F[k];
-    frame32[(size_t)k * n + c] = (float)F[k];
+    R[k] = F[k];
+    R32[k] = (float)F[k];
   }
+  R[15] = 0.0;
+  R32[15] = 0.0f;
   for (int k = 0; k < 3; ++k) {
     point[(size_t)k * n + c] = p[k];
     double xa = (a == M) ? 0.0 : pos[(size_t)k * M + a];
@@ -297,8 +302,10 @@ __global__ void k_gather(int n, int M, const int* __restrict__ perm2, const int*
     double vb = dsub(p[k], pos[(size_t)k * M + b]);
     arm_a[(size_t)k * n + c] = va;
     arm_b[(size_t)k * n + c] = vb;
-    arm_a32[(size_t)k * n + c] = (float)va;
-    arm_b32[(size_t)k * n + c] = (float)vb;
+    R[9 + k] = va;
+    R[12 + k] = vb;
+    R32[9 + k] = (float)va;
+    R32[12 + k] = (float)vb;
   }
 }
 
@@ -487,17 +494,16 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   c->arm_b.ensure(3 * n * sizeof(double));
   c->key.ensure(n * sizeof(unsigned long long));
   c->r.ensure((size_t)P * sizeof(double));
-  c->frame32.ensure(9 * n * sizeof(float));
-  c->arm_a32.ensure(3 * n * sizeof(float));
-  c->arm_b32.ensure(3 * n * sizeof(float));
+  c->rec64.ensure(16 * n * sizeof(double));
+  c->rec32.ensure(16 * n * sizeof(float));
   c->inv_m.ensure((size_t)M * sizeof(double));
   c->inv_I.ensure((size_t)M * sizeof(double));
   c->inv_m32.ensure((size_t)M * sizeof(float));
   c->inv_I32.ensure((size_t)M * sizeof(float));
   c->bptr.ensure(((size_t)M + 1) * sizeof(int));
   c->inc.ensure(2 * n * sizeof(int));
-  c->wbody.ensure(6 * (size_t)M * sizeof(double));
-  c->wbody32.ensure(6 * (size_t)M * sizeof(float));
+  c->wbody.ensure(8 * (size_t)M * sizeof(double));
+  c->wbody32.ensure(8 * (size_t)M * sizeof(float));
   c->H.ensure(6 * n * sizeof(double));
   c->H32.ensure(6 * n * sizeof(float));
   c->dinv.ensure((size_t)P * sizeof(double));
@@ -533,8 +539,8 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
     k_gather<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, M, i3, i1, wa, wb, phi_raw, nrm_raw, pt_raw, s->pos,
                                               c->ca.as<int>(), c->cb.as<int>(), c->phi.as<double>(),
                                               c->frame.as<double>(), c->point.as<double>(), c->arm_a.as<double>(),
-                                              c->arm_b.as<double>(), c->frame32.as<float>(),
-                                              c->arm_a32.as<float>(), c->arm_b32.as<float>());
+                                              c->arm_b.as<double>(), c->rec64.as<double>(),
+                                              c->rec32.as<float>());
     QP_CUDA(cudaMemcpyAsync(c->key.p, k2s, sizeof(unsigned long long) * (size_t)Nc, cudaMemcpyDeviceToDevice, st));
     QP_CUDA(cudaGetLastError());
   }

@@ -41,9 +41,7 @@ SysView<double> view64(qp_ctx* c, bool with_H) {
   v.P = c->P;
   v.ca = c->ca.as<int>();
   v.cb = c->cb.as<int>();
-  v.U = c->frame.as<double>();
-  v.ra = c->arm_a.as<double>();
-  v.rb = c->arm_b.as<double>();
+  v.rec = c->rec64.as<double>();
   v.inv_m = c->inv_m.as<double>();
   v.inv_I = c->inv_I.as<double>();
   v.bptr = c->bptr.as<int>();
@@ -61,9 +59,7 @@ SysView<float> view32(qp_ctx* c, bool with_H) {
   v.P = c->P;
   v.ca = c->ca.as<int>();
   v.cb = c->cb.as<int>();
-  v.U = c->frame32.as<float>();
-  v.ra = c->arm_a32.as<float>();
-  v.rb = c->arm_b32.as<float>();
+  v.rec = c->rec32.as<float>();
   v.inv_m = c->inv_m32.as<float>();
   v.inv_I = c->inv_I32.as<float>();
   v.bptr = c->bptr.as<int>();
@@ -122,13 +118,16 @@ int qp_destroy(qp_ctx_t c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   Buf* bufs[] = {&c->ca, &c->cb, &c->phi, &c->frame, &c->point, &c->arm_a, &c->arm_b, &c->key, &c->r,
-                 &c->frame32, &c->arm_a32, &c->arm_b32, &c->inv_m, &c->inv_I, &c->inv_m32, &c->inv_I32,
+                 &c->rec64, &c->rec32, &c->inv_m, &c->inv_I, &c->inv_m32, &c->inv_I32,
                  &c->bptr, &c->inc, &c->wbody, &c->wbody32, &c->H, &c->H32, &c->dinv, &c->dinv32,
                  &c->partial, &c->ctl};
   for (Buf* b : bufs) b->release();
   for (auto& b : c->v64) b.release();
   for (auto& b : c->v32) b.release();
   for (auto& b : c->scratch) b.release();
+  for (auto& b : c->la) b.release();
+  for (auto& b : c->dm) b.release();
+  if (c->last_inv) qtt_free(c, c->last_inv);
   if (c->ctl_host) cudaFreeHost(c->ctl_host);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

@@ -49,6 +49,9 @@ struct DevCtl {
   int outer;               // refinement steps
   int halvings;
   double scal[16];         // scalars handed between kernels (eta, t, s, norms, ...)
+  unsigned int release;    // flag barrier: generation released by block 0
+  unsigned int pad_[31];
+  unsigned int flags[4096];// flag barrier: generation reached by each block
 };
 
 enum Scal { S_ETA = 0, S_T, S_RDUAL, S_RT, S_S, S_RELRES, S_BNORM, S_SMAX, S_RCENT };
@@ -82,7 +85,7 @@ struct qp_ctx {
 
   // contact arrays (FP64 master + FP32 copies for the mixed-precision path)
   qp::Buf ca, cb, phi, frame, point, arm_a, arm_b, key, r;
-  qp::Buf frame32, arm_a32, arm_b32;
+  qp::Buf rec64, rec32;  // [Nc][16] contact records: n t1 t2 ra rb pad
   // body arrays
   qp::Buf inv_m, inv_I, inv_m32, inv_I32, bptr, inc;
   // operator work
@@ -92,9 +95,12 @@ struct qp_ctx {
   qp::Buf partial;     // per-block partial sums
   qp::Buf ctl;         // DevCtl
   qp::Buf scratch[8];  // assembly / QTT scratch
+  qp::Buf la[6];       // one-block linear algebra workspaces (A, V, Vs, w, tmp, misc)
+  qp::Buf dm[16];      // QTT inverse workspaces
   qp::DevCtl* ctl_host = nullptr;  // pinned mirror
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  qp_qtt* last_inv = nullptr;  // last QTT inverse built by pdip_step (warm start of the next)
 };
 
 namespace qp {
@@ -108,15 +114,13 @@ struct SysView {
   long long P;
   const int* ca;
   const int* cb;
-  const T* U;      // [9][Nc]  n, t1, t2
-  const T* ra;     // [3][Nc]
-  const T* rb;     // [3][Nc]
+  const T* rec;    // [Nc][16] contact records: n(3) t1(3) t2(3) ra(3) rb(3) 0
   const T* inv_m;  // [M]
   const T* inv_I;  // [M]
   const int* bptr; // [M+1]
   const int* inc;  // [2Nc] (contact << 1) | side, side 1 = body b
   const T* H;      // [6][Nc] packed 3x3 blocks (00 01 02 11 12 22) or null
-  T* w;            // [6][M] body scratch
+  T* w;            // [M][8] body scratch: M^-1 (force, torque), 2 pad
 };
 
 SysView<double> view64(qp_ctx* c, bool with_H);

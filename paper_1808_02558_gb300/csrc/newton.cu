@@ -23,7 +23,7 @@
 namespace qp {
 namespace {
 
-constexpr int NT = 256;               // threads per block of the cooperative kernels
+constexpr int NT = 512;               // threads per block of the cooperative kernels
 constexpr int NRED = 8;               // reduction slots per block
 constexpr long long BARRIER_BUDGET = 4000000000LL;  // clock64 ticks (~2 s) per barrier wait
 
@@ -31,33 +31,62 @@ constexpr long long BARRIER_BUDGET = 4000000000LL;  // clock64 ticks (~2 s) per 
 // Grid barrier with a bounded wait: on expiry it records QP_TIMEOUT in ctl->err
 // and returns false; callers leave the kernel.  Also returns false once any
 // block has recorded an error.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Flag barrier: block i publishes generation g in flags[i]; block 0 waits for
+// every flag (one polling thread per block), then publishes g in `release`,
+// which the other blocks poll.  No two blocks write the same word, so arrivals
+// do not serialise on an atomic.  Every wait is bounded by BARRIER_BUDGET; on
+// expiry QP_TIMEOUT is recorded and false is returned.
 __device__ bool grid_barrier(DevCtl* ctl, unsigned nblocks) {
   __shared__ int ok;
+  __shared__ unsigned gen_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &ctl->bar_gen;
-    unsigned gen = *vgen;
+    gen_s = ld_acquire(&ctl->flags[blockIdx.x]) + 1u;
     __threadfence();
-    unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-    int good = 1;
-    if (arrived == nblocks - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
+    st_release(&ctl->flags[blockIdx.x], gen_s);
+    ok = 1;
+  }
+  __syncthreads();
+  const unsigned gen = gen_s;
+  if (blockIdx.x == 0) {
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
       long long t0 = clock64();
-      while (*vgen == gen) {
+      while ((int)(ld_acquire(&ctl->flags[b]) - gen) < 0) {
         if (clock64() - t0 > BARRIER_BUDGET) {
           atomicCAS(&ctl->err, 0, QP_TIMEOUT);
-          good = 0;
+          ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(&ctl->release, gen);
+    }
+  } else if (threadIdx.x == 0) {
+    long long t0 = clock64();
+    while ((int)(ld_acquire(&ctl->release) - gen) < 0) {
+      if (clock64() - t0 > BARRIER_BUDGET) {
+        atomicCAS(&ctl->err, 0, QP_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
     __threadfence();
-    if (*(volatile int*)&ctl->err) good = 0;
-    ok = good;
+    if (*(volatile int*)&ctl->err) ok = 0;
   }
   __syncthreads();
   return ok != 0;
@@ -113,27 +142,84 @@ __device__ double grid_total(const double* partial, int slot, bool is_min = fals
 }
 
 // ------------------------------------------------------------------ operator
+// Contact record c (16 values): n(3) t1(3) t2(3) ra(3) rb(3) 0.  Body
+// intermediate w_b (8 values): M^-1 force (3), I^-1 torque (3), 2 pad.
+__device__ __forceinline__ void load_rec(const float* rec, int c, float (&v)[16]) {
+  const float4* p = reinterpret_cast<const float4*>(rec + (size_t)c * 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float4 q = __ldg(p + k);
+    v[4 * k] = q.x;
+    v[4 * k + 1] = q.y;
+    v[4 * k + 2] = q.z;
+    v[4 * k + 3] = q.w;
+  }
+}
+__device__ __forceinline__ void load_rec(const double* rec, int c, double (&v)[16]) {
+  const double2* p = reinterpret_cast<const double2*>(rec + (size_t)c * 16);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    double2 q = __ldg(p + k);
+    v[2 * k] = q.x;
+    v[2 * k + 1] = q.y;
+  }
+}
+__device__ __forceinline__ void load_w(const float* w, int b, float (&v)[6]) {
+  const float4* p = reinterpret_cast<const float4*>(w + (size_t)b * 8);
+  float4 a = p[0], q = p[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = q.x; v[5] = q.y;
+}
+__device__ __forceinline__ void load_w(const double* w, int b, double (&v)[6]) {
+  const double2* p = reinterpret_cast<const double2*>(w + (size_t)b * 8);
+  double2 a = p[0], q = p[1], r = p[2];
+  v[0] = a.x; v[1] = a.y; v[2] = q.x; v[3] = q.y; v[4] = r.x; v[5] = r.y;
+}
+__device__ __forceinline__ void store_w(float* w, int b, const float (&v)[6]) {
+  float4* p = reinterpret_cast<float4*>(w + (size_t)b * 8);
+  p[0] = make_float4(v[0], v[1], v[2], v[3]);
+  p[1] = make_float4(v[4], v[5], 0.f, 0.f);
+}
+__device__ __forceinline__ void store_w(double* w, int b, const double (&v)[6]) {
+  double2* p = reinterpret_cast<double2*>(w + (size_t)b * 8);
+  p[0] = make_double2(v[0], v[1]);
+  p[1] = make_double2(v[2], v[3]);
+  p[2] = make_double2(v[4], v[5]);
+}
+
+// Operand of the gather: x itself (beta == 0 and xprev == null) or the search
+// direction z + beta * xprev formed on the fly.
 template <class T>
-__device__ __forceinline__ void body_gather(const SysView<T>& s, const T* x, int b) {
+struct Operand {
+  const T* z;
+  const T* prev;
+  T beta;
+  __device__ __forceinline__ T operator()(long long i) const {
+    return prev ? z[i] + beta * prev[i] : z[i];
+  }
+};
+
+// w_b = M_b^-1 sum_{c in b} D_cb x_c   (force and torque of body b)
+template <class T, class X>
+__device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int b) {
   T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
-  const int e = s.bptr[b + 1];
-  const long long n = s.Nc;
-  for (int k = s.bptr[b]; k < e; ++k) {
+  const int e = __ldg(s.bptr + b + 1);
+#pragma unroll 2
+  for (int k = __ldg(s.bptr + b); k < e; ++k) {
     const int code = __ldg(s.inc + k);
     const int c = code >> 1;
     const long long row = (long long)s.slots * c;
-    const T x0 = x[row], x1 = x[row + 1], x2 = x[row + 2];
-    const T* U = s.U;
-    T f0 = __ldg(U + c) * x0 + __ldg(U + 3 * n + c) * x1 + __ldg(U + 6 * n + c) * x2;
-    T f1 = __ldg(U + n + c) * x0 + __ldg(U + 4 * n + c) * x1 + __ldg(U + 7 * n + c) * x2;
-    T f2 = __ldg(U + 2 * n + c) * x0 + __ldg(U + 5 * n + c) * x1 + __ldg(U + 8 * n + c) * x2;
-    const T* arm = (code & 1) ? s.rb : s.ra;
-    const T a0 = __ldg(arm + c), a1 = __ldg(arm + n + c), a2 = __ldg(arm + 2 * n + c);
-    if (!(code & 1)) {
-      f0 = -f0;
-      f1 = -f1;
-      f2 = -f2;
-    }
+    T R[16];
+    load_rec(s.rec, c, R);
+    const T x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
+    T f0 = R[0] * x0 + R[3] * x1 + R[6] * x2;
+    T f1 = R[1] * x0 + R[4] * x1 + R[7] * x2;
+    T f2 = R[2] * x0 + R[5] * x1 + R[8] * x2;
+    const bool side_b = (code & 1) != 0;
+    const T a0 = side_b ? R[12] : R[9], a1 = side_b ? R[13] : R[10], a2 = side_b ? R[14] : R[11];
+    const T sg = side_b ? T(1) : T(-1);
+    f0 *= sg;
+    f1 *= sg;
+    f2 *= sg;
     F0 += f0;
     F1 += f1;
     F2 += f2;
@@ -142,39 +228,36 @@ __device__ __forceinline__ void body_gather(const SysView<T>& s, const T* x, int
     Q2 += a0 * f1 - a1 * f0;
   }
   const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
-  const long long M = s.M;
-  s.w[b] = im * F0;
-  s.w[M + b] = im * F1;
-  s.w[2 * M + b] = im * F2;
-  s.w[3 * M + b] = iI * Q0;
-  s.w[4 * M + b] = iI * Q1;
-  s.w[5 * M + b] = iI * Q2;
+  T v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
+  store_w(s.w, b, v);
 }
 
-// y_c = U^T [(v_b + w_b x rb) - (v_a + w_a x ra)] + H_c x_c ; returns x_c . y_c
-template <class T>
-__device__ __forceinline__ double contact_apply(const SysView<T>& s, const T* x, T* y, int c) {
-  const long long n = s.Nc, M = s.M;
+// y_c = U^T [(v_b + w_b x rb) - (v_a + w_a x ra)] + H_c x_c ; returns x_c . y_c.
+// If xout is set, the operand value of row i is also stored there (the
+// materialised search direction).
+template <class T, class X>
+__device__ __forceinline__ double contact_apply(const SysView<T>& s, const X& x, T* y, int c, T* xout = nullptr) {
+  const long long n = s.Nc;
   const int a = __ldg(s.ca + c), b = __ldg(s.cb + c);
-  const T* w = s.w;
-  T rb0 = __ldg(s.rb + c), rb1 = __ldg(s.rb + n + c), rb2 = __ldg(s.rb + 2 * n + c);
-  T wb0 = w[3 * M + b], wb1 = w[4 * M + b], wb2 = w[5 * M + b];
-  T d0 = w[b] + (wb1 * rb2 - wb2 * rb1);
-  T d1 = w[M + b] + (wb2 * rb0 - wb0 * rb2);
-  T d2 = w[2 * M + b] + (wb0 * rb1 - wb1 * rb0);
+  T R[16];
+  load_rec(s.rec, c, R);
+  T wb[6];
+  load_w(s.w, b, wb);
+  T d0 = wb[0] + (wb[4] * R[14] - wb[5] * R[13]);
+  T d1 = wb[1] + (wb[5] * R[12] - wb[3] * R[14]);
+  T d2 = wb[2] + (wb[3] * R[13] - wb[4] * R[12]);
   if (a < s.M) {
-    T ra0 = __ldg(s.ra + c), ra1 = __ldg(s.ra + n + c), ra2 = __ldg(s.ra + 2 * n + c);
-    T wa0 = w[3 * M + a], wa1 = w[4 * M + a], wa2 = w[5 * M + a];
-    d0 -= w[a] + (wa1 * ra2 - wa2 * ra1);
-    d1 -= w[M + a] + (wa2 * ra0 - wa0 * ra2);
-    d2 -= w[2 * M + a] + (wa0 * ra1 - wa1 * ra0);
+    T wa[6];
+    load_w(s.w, a, wa);
+    d0 -= wa[0] + (wa[4] * R[11] - wa[5] * R[10]);
+    d1 -= wa[1] + (wa[5] * R[9] - wa[3] * R[11]);
+    d2 -= wa[2] + (wa[3] * R[10] - wa[4] * R[9]);
   }
-  const T* U = s.U;
   const long long row = (long long)s.slots * c;
-  const T x0 = x[row], x1 = x[row + 1], x2 = x[row + 2];
-  T y0 = __ldg(U + c) * d0 + __ldg(U + n + c) * d1 + __ldg(U + 2 * n + c) * d2;
-  T y1 = __ldg(U + 3 * n + c) * d0 + __ldg(U + 4 * n + c) * d1 + __ldg(U + 5 * n + c) * d2;
-  T y2 = __ldg(U + 6 * n + c) * d0 + __ldg(U + 7 * n + c) * d1 + __ldg(U + 8 * n + c) * d2;
+  const T x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
+  T y0 = R[0] * d0 + R[1] * d1 + R[2] * d2;
+  T y1 = R[3] * d0 + R[4] * d1 + R[5] * d2;
+  T y2 = R[6] * d0 + R[7] * d1 + R[8] * d2;
   if (s.H) {
     const T* H = s.H;
     T h00 = __ldg(H + c), h01 = __ldg(H + n + c), h02 = __ldg(H + 2 * n + c);
@@ -187,22 +270,34 @@ __device__ __forceinline__ double contact_apply(const SysView<T>& s, const T* x,
   y[row + 1] = y1;
   y[row + 2] = y2;
   double dot = (double)x0 * (double)y0 + (double)x1 * (double)y1 + (double)x2 * (double)y2;
+  if (xout) {
+    xout[row] = x0;
+    xout[row + 1] = x1;
+    xout[row + 2] = x2;
+  }
   if (s.slots == 4) {
-    y[row + 3] = x[row + 3];
-    dot += (double)x[row + 3] * (double)x[row + 3];
+    const T x3 = x(row + 3);
+    y[row + 3] = x3;
+    if (xout) xout[row + 3] = x3;
+    dot += (double)x3 * (double)x3;
   }
   return dot;
 }
 
 template <class T>
+__device__ __forceinline__ Operand<T> plain(const T* x) {
+  return Operand<T>{x, nullptr, T(0)};
+}
+
+template <class T>
 __global__ void k_body_gather(SysView<T> s, const T* x) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < s.M; b += gridDim.x * blockDim.x) body_gather(s, x, b);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < s.M; b += gridDim.x * blockDim.x) body_gather(s, plain(x), b);
 }
 
 template <class T>
 __global__ void k_contact_apply(SysView<T> s, const T* x, T* y) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.Nc; c += gridDim.x * blockDim.x)
-    contact_apply(s, x, y, c);
+    contact_apply(s, plain(x), y, c);
   // dummy tail rows: identity
   const long long tail0 = (long long)s.slots * s.Nc;
   for (long long i = tail0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.P;
@@ -299,6 +394,11 @@ __device__ bool qtt_precond(const PcgArgs& A, const T* r, T* z) {
 
 // Inner PCG on S_T e = b (x0 = 0) to ||b - S e|| <= tol ||b||.  Returns
 // 0 converged, 1 cap reached, 2 breakdown, -1 barrier failure.
+//
+// Three grid barriers per iteration: the search direction p_k = z + beta p_{k-1}
+// is never materialised before the operator: the body gather forms it on the
+// fly from (z, p_{k-1}), and the contact pass stores it into the other p buffer
+// while it computes q = S p_k.
 template <class T, class TC>
 __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   const SysView<T>& s = sys_of<T>(A);
@@ -306,7 +406,8 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   T* e = static_cast<T*>(A.e);
   T* r = static_cast<T*>(A.r);
   T* z = static_cast<T*>(A.z);
-  T* p = static_cast<T*>(A.p);
+  T* pa = static_cast<T*>(A.p);
+  T* pb = static_cast<T*>(A.q) + A.P;  // second search-direction buffer
   T* q = static_cast<T*>(A.q);
   const T* dinv = static_cast<const T*>(A.dinv);
   const long long gsz = (long long)gridDim.x * blockDim.x;
@@ -314,7 +415,7 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   const int nrow = A.nrow;
   const unsigned nb = gridDim.x;
 
-  // setup: e = 0, r = b, z = M^-1 r, p = z
+  // setup: e = 0, r = b, z = M^-1 r
   double acc[2] = {0.0, 0.0};
   for (long long i = tid; i < nrow; i += gsz) {
     T bi = b[i];
@@ -324,7 +425,6 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
     if (!A.use_qtt) {
       T zi = dinv[i] * bi;
       z[i] = zi;
-      p[i] = zi;
       acc[1] += (double)bi * (double)zi;
     }
   }
@@ -336,23 +436,23 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   if (A.use_qtt) {
     if (!qtt_precond<T, TC>(A, r, z)) return -1;
     double a1[1] = {0.0};
-    for (long long i = tid; i < nrow; i += gsz) {
-      T zi = z[i];
-      p[i] = zi;
-      a1[0] += (double)r[i] * (double)zi;
-    }
+    for (long long i = tid; i < nrow; i += gsz) a1[0] += (double)r[i] * (double)z[i];
     block_partials<1>(a1, A.partial, 1);
     if (!grid_barrier(A.ctl, nb)) return -1;
     rz = grid_total(A.partial, 1);
   }
   const double stop = tol * tol * bb;
+  T* pold = pa;   // p_{k-1} (unused while beta == 0)
+  T* pnew = pb;   // p_k, written by the contact pass
+  double beta = 0.0;
   for (int it = 0; it < maxit; ++it) {
     if (!(rz > 0.0)) return 2;
-    // q = S p
-    for (int bd = (int)tid; bd < s.M; bd += (int)gsz) body_gather(s, p, bd);
+    const Operand<T> dir{z, it == 0 ? nullptr : pold, (T)beta};
+    // q = S p_k
+    for (int bd = (int)tid; bd < s.M; bd += (int)gsz) body_gather(s, dir, bd);
     if (!grid_barrier(A.ctl, nb)) return -1;
     double a2[1] = {0.0};
-    for (int c = (int)tid; c < s.Nc; c += (int)gsz) a2[0] += contact_apply(s, p, q, c);
+    for (int c = (int)tid; c < s.Nc; c += (int)gsz) a2[0] += contact_apply(s, dir, q, c, pnew);
     block_partials<1>(a2, A.partial, 2);
     if (!grid_barrier(A.ctl, nb)) return -1;
     const double pq = grid_total(A.partial, 2);
@@ -360,7 +460,7 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
     const double alpha = rz / pq;
     double a3[2] = {0.0, 0.0};
     for (long long i = tid; i < nrow; i += gsz) {
-      T pi = p[i];
+      T pi = pnew[i];
       e[i] += (T)alpha * pi;
       T ri = r[i] - (T)alpha * q[i];
       r[i] = ri;
@@ -387,17 +487,18 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
     } else {
       rz_new = grid_total(A.partial, 4);
     }
-    const double beta = rz_new / rz;
+    beta = rz_new / rz;
     rz = rz_new;
-    for (long long i = tid; i < nrow; i += gsz) p[i] = z[i] + (T)beta * p[i];
-    if (!grid_barrier(A.ctl, nb)) return -1;
+    T* t = pold;
+    pold = pnew;
+    pnew = t;
   }
   return 1;
 }
 
 // FP64 outer refinement: r64 = rhs - S x; inner solve on r64/||r64||; x += ...
 template <class T, class TC>
-__global__ void __launch_bounds__(NT) k_pcg(PcgArgs A) {
+__global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -431,9 +532,9 @@ __global__ void __launch_bounds__(NT) k_pcg(PcgArgs A) {
           rr[0] += A.rhs[i] * A.rhs[i];
         }
       } else {
-        for (int bd = (int)tid; bd < s64.M; bd += (int)gsz) body_gather(s64, A.x, bd);
+        for (int bd = (int)tid; bd < s64.M; bd += (int)gsz) body_gather(s64, plain<double>(A.x), bd);
         if (!grid_barrier(A.ctl, nb)) return;
-        for (int c = (int)tid; c < s64.Nc; c += (int)gsz) contact_apply(s64, A.x, A.q64, c);
+        for (int c = (int)tid; c < s64.Nc; c += (int)gsz) contact_apply(s64, plain<double>(A.x), A.q64, c);
         if (!grid_barrier(A.ctl, nb)) return;
         for (long long i = tid; i < A.nrow; i += gsz) {
           double ri = A.rhs[i] - A.q64[i];
@@ -485,16 +586,16 @@ __global__ void k_diag(SysView<double> s, const double* __restrict__ H, double* 
     int u = (int)(i - c * s.slots);
     double v = 1.0;
     if (c < n && u < 3) {
-      double U0 = s.U[(3 * u) * n + c], U1 = s.U[(3 * u + 1) * n + c], U2 = s.U[(3 * u + 2) * n + c];
+      double R[16];
+      load_rec(s.rec, (int)c, R);
+      double U0 = R[3 * u], U1 = R[3 * u + 1], U2 = R[3 * u + 2];
       int a = s.ca[c], b = s.cb[c];
-      double rb0 = s.rb[c], rb1 = s.rb[n + c], rb2 = s.rb[2 * n + c];
-      double t0 = rb1 * U2 - rb2 * U1, t1 = rb2 * U0 - rb0 * U2, t2 = rb0 * U1 - rb1 * U0;
+      double t0 = R[13] * U2 - R[14] * U1, t1 = R[14] * U0 - R[12] * U2, t2 = R[12] * U1 - R[13] * U0;
       v = s.inv_m[b] + s.inv_I[b] * (t0 * t0 + t1 * t1 + t2 * t2);
       if (a < s.M) {
-        double ra0 = s.ra[c], ra1 = s.ra[n + c], ra2 = s.ra[2 * n + c];
-        t0 = ra1 * U2 - ra2 * U1;
-        t1 = ra2 * U0 - ra0 * U2;
-        t2 = ra0 * U1 - ra1 * U0;
+        t0 = R[10] * U2 - R[11] * U1;
+        t1 = R[11] * U0 - R[9] * U2;
+        t2 = R[9] * U1 - R[10] * U0;
         v += s.inv_m[a] + s.inv_I[a] * (t0 * t0 + t1 * t1 + t2 * t2);
       }
       if (H) v += H[(u == 0 ? 0 : (u == 1 ? 3 : 5)) * n + c];
@@ -527,7 +628,7 @@ struct PdipArgs {
 
 // gap, t, residual norms, Schur blocks and Newton rhs at (gamma, lambda).
 // mode 0: full pre-step; mode 1: only eta and ||r_dual|| (measurement).
-__global__ void __launch_bounds__(NT) k_pdip_pre(PdipArgs A, int mode) {
+__global__ void __launch_bounds__(NT, 1) k_pdip_pre(PdipArgs A, int mode) {
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -535,11 +636,11 @@ __global__ void __launch_bounds__(NT) k_pdip_pre(PdipArgs A, int mode) {
   SysView<double> s = A.s;
   s.H = nullptr;
   // N gamma
-  for (int b = tid; b < s.M; b += (int)gsz) body_gather(s, A.gamma, b);
+  for (int b = tid; b < s.M; b += (int)gsz) body_gather(s, plain<double>(A.gamma), b);
   if (!grid_barrier(A.ctl, nb)) return;
   double acc[1] = {0.0};
   for (int c = tid; c < n; c += (int)gsz) {
-    contact_apply(s, A.gamma, A.Ng, c);
+    contact_apply(s, plain<double>(A.gamma), A.Ng, c);
     const long long row = (long long)A.slots * c;
     double gn = A.gamma[row], g1 = A.gamma[row + 1], g2 = A.gamma[row + 2];
     double fc = 0.5 * (g1 * g1 + g2 * g2 - A.mu * A.mu * gn * gn);
@@ -593,7 +694,7 @@ __global__ void __launch_bounds__(NT) k_pdip_pre(PdipArgs A, int mode) {
 // dlambda, ratio test, backtracking (feasibility, then sufficient decrease of
 // ||r_t||), update.  Every block evaluates the same reduced scalars, so all
 // blocks take the same branches.
-__global__ void __launch_bounds__(NT) k_pdip_post(PdipArgs A) {
+__global__ void __launch_bounds__(NT, 1) k_pdip_post(PdipArgs A) {
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -604,11 +705,11 @@ __global__ void __launch_bounds__(NT) k_pdip_post(PdipArgs A) {
   SysView<double> s = A.s;
   s.H = nullptr;
   // N dg
-  for (int b = tid; b < s.M; b += (int)gsz) body_gather(s, A.dg, b);
+  for (int b = tid; b < s.M; b += (int)gsz) body_gather(s, plain<double>(A.dg), b);
   if (!grid_barrier(A.ctl, nb)) return;
   double mn[1] = {1e300};
   for (int c = tid; c < n; c += (int)gsz) {
-    contact_apply(s, A.dg, A.NDg, c);
+    contact_apply(s, plain<double>(A.dg), A.NDg, c);
     const long long row = (long long)A.slots * c;
     double gn = A.gamma[row], g1 = A.gamma[row + 1], g2 = A.gamma[row + 2];
     double d0 = A.dg[row], d1 = A.dg[row + 1], d2 = A.dg[row + 2];
@@ -710,7 +811,8 @@ int coop_grid(qp_ctx* c, K kernel) {
   int per_sm = 0;
   QP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, 0));
   QP_REQUIRE(per_sm > 0, QP_CUDA_ERROR, "cooperative kernel does not fit on an SM");
-  if (per_sm > 4) per_sm = 4;
+  if (per_sm > 2) per_sm = 2;
+  QP_REQUIRE(per_sm * c->num_sms <= 4096, QP_INVALID_ARG, "grid larger than the barrier flag array");
   return per_sm * c->num_sms;
 }
 
@@ -835,7 +937,7 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   A.r = (mixed ? c->v32[2] : c->scratch[2]).ensure(P * es);
   A.z = (mixed ? c->v32[3] : c->scratch[3]).ensure(P * es);
   A.p = (mixed ? c->v32[4] : c->scratch[4]).ensure(P * es);
-  A.q = (mixed ? c->v32[5] : c->v64[7]).ensure(P * es);
+  A.q = (mixed ? c->v32[5] : c->v64[7]).ensure(2 * P * es);  // q and the second search direction
   A.dinv = mixed ? (const void*)c->dinv32.p : (const void*)c->dinv.p;
   A.use_qtt = use_qtt ? 1 : 0;
   A.qw0 = A.qw1 = nullptr;
@@ -991,20 +1093,25 @@ int pdip_step(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, qp_pdip_stats* st
   out.r_t = h.scal[S_RT];
   st->t = out.t;
   qp_solve_opts so = o->solve;
-  qtt_t X = nullptr;
   if (o->qtt_refresh && so.precond == QP_QTT_PCG) {
-    cudaEvent_t e0 = c->ev0, e1 = c->ev1;
-    QP_CUDA(cudaEventRecord(e0, c->stream));
+    // compress S_k and invert it, warm-started from the previous inverse
+    // (Sec. 3.3: S_{k+1} = S_k + L_k with L_k block diagonal)
+    QP_CUDA(cudaEventRecord(c->ev0, c->stream));
     qtt_t S = nullptr;
     int rc = qtt_compress(c, st, o->qtt_eps, o->qtt_rmax, &S);
     if (rc != QP_OK) throw Error{rc, "pdip_step: qtt_compress failed: " + c->last_error};
-    rc = qtt_inverse(c, S, o->qtt_eps, o->qtt_rmax, 4, so.X, &X);
+    qtt_t warm = so.X ? so.X : c->last_inv;
+    if (warm && warm->d != S->d) warm = nullptr;
+    qtt_t X = nullptr;
+    rc = qtt_inverse(c, S, o->qtt_eps, o->qtt_rmax, warm ? 2 : 4, warm, &X);
     qtt_free(c, S);
     if (rc != QP_OK) throw Error{rc, "pdip_step: qtt_inverse failed: " + c->last_error};
-    QP_CUDA(cudaEventRecord(e1, c->stream));
-    QP_CUDA(cudaEventSynchronize(e1));
+    if (c->last_inv) qtt_free(c, c->last_inv);
+    c->last_inv = X;
+    QP_CUDA(cudaEventRecord(c->ev1, c->stream));
+    QP_CUDA(cudaEventSynchronize(c->ev1));
     float ms = 0;
-    QP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    QP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     out.ms_refresh = ms;
     so.X = X;
   }
@@ -1016,7 +1123,6 @@ int pdip_step(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, qp_pdip_stats* st
   A.max_halvings = o->max_halvings;
   // H blocks were built by the pre-step
   out.solve = solve(c, A.rhs, A.dg, &so);
-  if (X) qtt_free(c, X);
   if (out.solve.status == QP_TIMEOUT) throw Error{QP_TIMEOUT, "pdip_step: Krylov barrier wait expired"};
   // keep t in the control block for the post-step
   reset_ctl(c);

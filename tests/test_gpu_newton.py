@@ -132,3 +132,27 @@ def test_solve_zero_rhs(pile8):
     dx = torch.full_like(rhs, 7.0)
     stats = pile8.ctx.newton_solve(st, rhs, dx, pile8.ctx.solve_opts(tol=1e-10), allow=())
     assert stats.iters == 0 and torch.count_nonzero(dx).item() == 0
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_solve_qtt_preconditioned(pile8, mixed):
+    """QTT-PCG (Sec. 3.3): S compressed and inverted in QTT, applied inside the PCG."""
+    g, lam = pile8.iters[3]
+    gd, ld, st = pile8.state(g, lam)
+    rhs = torch.empty(pile8.P, dtype=torch.float64, device="cuda")
+    pile8.ctx.newton_rhs(st, rhs)
+    S_tt = pile8.ctx.qtt_compress(st, 1e-2, 10)
+    X = pile8.ctx.qtt_inverse(S_tt, 1e-2, 10, sweeps=3)
+    dx = torch.empty_like(rhs)
+    opts = pile8.ctx.solve_opts(binding.QP_QTT_PCG, X, tol=1e-10, maxit=20000, mixed=mixed,
+                                inner_tol=1e-3 if mixed else 0.0, max_outer=60,
+                                core_dtype=binding.QP_BF16 if mixed else binding.QP_F32)
+    stats = pile8.ctx.newton_solve(st, rhs, dx, opts, allow=())
+    S = qp.schur_matrix(pile8.N, g, lam, pile8.scene.mu)
+    b = pile8.unpad(to_np(rhs))
+    res = np.linalg.norm(b - S @ pile8.unpad(to_np(dx))) / np.linalg.norm(b)
+    assert res <= 1.05e-10 and stats.rel_res <= 1e-10
+    jac = pile8.ctx.newton_solve(st, rhs, torch.empty_like(rhs),
+                                 pile8.ctx.solve_opts(tol=1e-10, maxit=20000, mixed=mixed,
+                                                      inner_tol=1e-3 if mixed else 0.0, max_outer=60), allow=())
+    print(f"QTT-PCG iters {stats.iters} vs Jacobi-PCG {jac.iters} (mixed={mixed})")

@@ -80,3 +80,21 @@ def test_small_lattice_final_impulses(ctx):
     gg, _ = run_gpu_pdip(ctx, pb, res.iters)
     assert relerr(gg, res.gamma) <= 1e-6
     assert relerr(pb.D @ gg, pb.D @ res.gamma) <= 1e-6
+
+
+def test_single_step_with_qtt_refresh_matches_oracle(ctx):
+    """pdip_step with the QTT refresh (compress + invert + QTT-PCG) takes the oracle's step."""
+    pb = Problem(ctx, scene_for("pile8", 3))
+    g, lam = pb.oracle_iterates(2)
+    g1, l1, info = pdip.pdip_step(pb.N, pb.r, pb.scene.mu, g, lam)
+    gd, ld, st = pb.state(g, lam)
+    so = pb.ctx.solve_opts(binding.QP_QTT_PCG, None, tol=1e-12, maxit=100000)
+    opts = pb.ctx.pdip_opts(so, qtt_refresh=1, qtt_eps=1e-2, qtt_rmax=10)
+    stats = pb.ctx.pdip_step(st, opts, allow=())
+    assert stats.ms_refresh > 0
+    assert relerr(pb.unpad(to_np(gd)), g1) <= 1e-8
+    assert relerr(to_np(ld), l1) <= 1e-8
+    # second step warm-starts the inverse from the context's previous one
+    g2, l2, _ = pdip.pdip_step(pb.N, pb.r, pb.scene.mu, g1, l1)
+    pb.ctx.pdip_step(st, opts, allow=())
+    assert relerr(pb.unpad(to_np(gd)), g2) <= 1e-7

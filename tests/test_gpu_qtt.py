@@ -68,3 +68,135 @@ def test_apply_full_size_d20(ctx):
     y = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
     ctx.qtt_apply(A, dev(x), y)
     assert relerr(to_np(y), want) <= 1e-13
+
+
+# ---------------------------------------------------------------- rounding (Sec. 3.1)
+def test_round_sum_recovers_ranks(ctx):
+    rng = np.random.default_rng(7)
+    d = 9
+    A = rng.standard_normal((1 << d, 1 << d))
+    A = A @ A.T
+    cores = tt.qtt_compress_dense(A, 1e-3)
+    dbl = tt.tt_add(cores, cores)
+    G = ctx.qtt_from_cores(dbl)
+    # the one-block FP64 SVD works on Gram matrices: singular values below about
+    # 1e-8 sigma_max are not resolved, so exact rank recovery is checked at eps = 1e-6
+    R = ctx.qtt_round(G, 1e-6)
+    assert R.ranks() == tt.tt_ranks(cores)
+    want = 2 * tt.qtt_matrix(cores)
+    assert relerr(tt.qtt_matrix(R.cores()), want) <= 1e-6
+
+
+@pytest.mark.parametrize("eps,rmax", [(1e-1, 1000), (1e-2, 1000), (1e-2, 6), (1e-6, 1000)])
+def test_round_matches_oracle(ctx, eps, rmax):
+    rng = np.random.default_rng(11)
+    d = 8
+    cores = random_cores(d, 9, 3)
+    # a sum with redundant directions exercises rank-deficient orthogonalisation
+    big = tt.tt_add(cores, tt.tt_scale(random_cores(d, 5, 4), 0.3))
+    want = tt.tt_round(big, eps, rmax)
+    R = ctx.qtt_round(ctx.qtt_from_cores(big), eps, rmax)
+    assert R.ranks() == tt.tt_ranks(want)
+    full = tt.qtt_matrix(big)
+    got = tt.qtt_matrix(R.cores())
+    assert relerr(got, tt.qtt_matrix(want)) <= 1e-9
+    if rmax >= 1000:
+        assert np.linalg.norm(got - full) <= eps * np.linalg.norm(full) * (1 + 1e-9)
+
+
+# ---------------------------------------------------------------- compression (Alg. 1)
+def schur_dense(s, slots=3, k_iter=0):
+    con = oc.detect(s)
+    _, N, r = qp.qp_data(s, con)
+    g, lam = qp.initial_point(con.Nc, s.mu)
+    L, P = qp.padded_size(con.Nc, slots)
+    S = qp.padded_matrix(qp.schur_matrix(N, g, lam, s.mu), con.Nc, slots, P).toarray()
+    Nd = qp.padded_matrix(N, con.Nc, slots, P).toarray()
+    return con, g, lam, S, Nd, P
+
+
+@pytest.mark.parametrize("slots", [3, 4])
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6])
+def test_compress_matches_oracle_ttsvd(eps, slots):
+    s = lattice_scene(3, 4, polydisperse=True)
+    con, g, lam, S, Nd, P = schur_dense(s, slots)
+    ctx = binding.Context()
+    from paper_1808_02558_gb300 import workload
+
+    workload.assemble(ctx, s, slots)
+    gd = dev(qp.to_padded(g, con.Nc, slots, P))
+    ld = dev(lam)
+    st = ctx.state(gd, ld)
+    for A_dense, state in ((S, st), (Nd, None)):
+        want = tt.qtt_compress_dense(A_dense, eps, 100, reverse=True)
+        X = ctx.qtt_compress(state, eps, 100)
+        got = tt.qtt_matrix(X.cores())
+        assert X.ranks() == tt.tt_ranks(want)
+        assert relerr(got, tt.qtt_matrix(want)) <= 1e-9
+        if max(X.ranks()) < 100:
+            assert np.linalg.norm(got - A_dense) <= eps * np.linalg.norm(A_dense) * (1 + 1e-9)
+
+
+def test_compress_rank_cap_and_probe_full_size():
+    from paper_1808_02558_gb300 import workload
+    from synth import random_vector, scene_for
+
+    s = scene_for("pile20", 1)
+    ctx = binding.Context()
+    _, con = workload.assemble(ctx, s)
+    o = oc.detect(s)
+    _, N, _ = qp.qp_data(s, o)
+    g, lam = qp.initial_point(o.Nc, s.mu)
+    L, P = qp.padded_size(o.Nc, 3)
+    st = ctx.state(dev(qp.to_padded(g, o.Nc, 3, P)), dev(lam))
+    X = ctx.qtt_compress(st, 1e-2, 10)
+    assert max(X.ranks()) <= 10 and X.d == 17
+    # probe ||(S - S_TT) z|| / ||S z|| with the oracle's S and the library's QTT apply
+    S = qp.padded_matrix(qp.schur_matrix(N, g, lam, s.mu), o.Nc, 3, P)
+    z = random_vector(3, 2, P)
+    y = torch.empty(P, dtype=torch.float64, device="cuda")
+    ctx.qtt_apply(X, dev(z), y)
+    err = np.linalg.norm(to_np(y) - S @ z) / np.linalg.norm(S @ z)
+    assert err < 0.5, err
+
+
+# ---------------------------------------------------------------- inverse (Sec. 3.2, 3.3)
+def test_inverse_tridiagonal_toeplitz(ctx):
+    d = 8
+    n = 1 << d
+    T = 2.5 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    S = ctx.qtt_from_cores(tt.qtt_compress_dense(T, 1e-14))
+    X = ctx.qtt_inverse(S, 1e-6, 40, sweeps=4)
+    Xd = tt.qtt_matrix(X.cores())
+    Tinv = np.linalg.inv(T)
+    assert relerr(Xd, Tinv) <= 1e-4
+    # symmetrised then rounded: symmetric up to the rounding accuracy
+    assert np.linalg.norm(Xd - Xd.T) <= 1e-5 * np.linalg.norm(Xd)
+    # warm start from the previous inverse of a perturbed matrix (Sec. 3.3 inverse update)
+    T2 = T + 0.05 * np.diag(np.cos(np.arange(n)))
+    S2 = ctx.qtt_from_cores(tt.qtt_compress_dense(T2, 1e-14))
+    X2 = ctx.qtt_inverse(S2, 1e-6, 40, sweeps=2, warm=X)
+    assert relerr(tt.qtt_matrix(X2.cores()), np.linalg.inv(T2)) <= 1e-3
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-3])
+def test_inverse_of_compressed_schur_matrix(eps):
+    from paper_1808_02558_gb300 import workload
+
+    s = lattice_scene(3, 4, polydisperse=True)
+    con, g, lam, Sd, Nd, P = schur_dense(s, 3)
+    ctx = binding.Context()
+    workload.assemble(ctx, s, 3)
+    st = ctx.state(dev(qp.to_padded(g, con.Nc, 3, P)), dev(lam))
+    STT = ctx.qtt_compress(st, 1e-10, 128)
+    X = ctx.qtt_inverse(STT, eps, 64, sweeps=4)
+    Xd = tt.qtt_matrix(X.cores())
+    Sinv = np.linalg.inv(Sd)
+    # this 2^8 matrix is barely compressible: compare with the TT-SVD of the exact
+    # inverse under the same rank cap (the best the format allows)
+    ref = tt.qtt_matrix(tt.qtt_inverse_dense(Sd, eps, 64))
+    err = relerr(Xd, Sinv)
+    best = relerr(ref, Sinv)
+    # two-site sweeps truncate every split at eps locally; at eps = 1e-2 the sweep
+    # result sits within a small factor of the best approximation
+    assert err <= 4 * max(best, eps), (err, best)
