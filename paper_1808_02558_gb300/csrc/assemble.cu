@@ -566,6 +566,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   QP_CUDA(cudaGetLastError());
   QP_CUDA(cudaStreamSynchronize(st));
   c->have_contacts = true;
+  c->part_G = 0;  // the Krylov partition follows the contact set
 
   out->M = M;
   out->Nc = Nc;

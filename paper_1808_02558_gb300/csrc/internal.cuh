@@ -101,6 +101,9 @@ struct qp_ctx {
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   qp_qtt* last_inv = nullptr;  // last QTT inverse built by pdip_step (warm start of the next)
+  // contact partition of the fused Krylov kernel (one contiguous chunk per block)
+  int part_G = 0, part_chunk = 0, part_maxb = 0, part_nbmax = 0;
+  qp::Buf part_nb, part_bodies, part_cl;
 };
 
 namespace qp {

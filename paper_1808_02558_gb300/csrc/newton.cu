@@ -15,7 +15,9 @@
 //    post-step (dlambda, ratio test, backtracking, update) as cooperative kernels.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "internal.cuh"
 #include "qtt_dev.cuh"
@@ -24,7 +26,10 @@ namespace qp {
 namespace {
 
 constexpr int NT = 512;               // threads per block of the cooperative kernels
-constexpr int NRED = 8;               // reduction slots per block
+constexpr int NT_FUSED = 512;         // threads per block of the fused pipelined kernel
+constexpr int FUSED_MAX_CHUNK = 512;  // contacts per block up to which the fused kernel is used
+constexpr int NWMAX = 32;             // warps per block at most
+constexpr int NRED = 16;              // reduction slots per block
 constexpr long long BARRIER_BUDGET = 4000000000LL;  // clock64 ticks (~2 s) per barrier wait
 
 // ------------------------------------------------------------------ barrier
@@ -104,7 +109,7 @@ __device__ __forceinline__ double warp_min(double v) {
 // Block-reduce n values (sum) and store them as this block's partials.
 template <int N>
 __device__ void block_partials(double (&v)[N], double* partial, int slot0, bool is_min = false) {
-  __shared__ double sm[N][NT / 32];
+  __shared__ double sm[N][NWMAX];
   for (int k = 0; k < N; ++k) {
     double x = is_min ? warp_min(v[k]) : warp_sum(v[k]);
     if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = x;
@@ -112,7 +117,7 @@ __device__ void block_partials(double (&v)[N], double* partial, int slot0, bool 
   __syncthreads();
   if (threadIdx.x < N) {
     double x = sm[threadIdx.x][0];
-    for (int w = 1; w < NT / 32; ++w) x = is_min ? fmin(x, sm[threadIdx.x][w]) : x + sm[threadIdx.x][w];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = is_min ? fmin(x, sm[threadIdx.x][w]) : x + sm[threadIdx.x][w];
     partial[(size_t)blockIdx.x * NRED + slot0 + threadIdx.x] = x;
   }
   __syncthreads();
@@ -120,7 +125,7 @@ __device__ void block_partials(double (&v)[N], double* partial, int slot0, bool 
 
 // Sum (or min) of one partial slot over all blocks, same value in every block.
 __device__ double grid_total(const double* partial, int slot, bool is_min = false) {
-  __shared__ double sm[NT / 32];
+  __shared__ double sm[NWMAX];
   __shared__ double res;
   double x = is_min ? 1e300 : 0.0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
@@ -132,7 +137,7 @@ __device__ double grid_total(const double* partial, int slot, bool is_min = fals
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = sm[0];
-    for (int w = 1; w < NT / 32; ++w) t = is_min ? fmin(t, sm[w]) : t + sm[w];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = is_min ? fmin(t, sm[w]) : t + sm[w];
     res = t;
   }
   __syncthreads();
@@ -576,6 +581,475 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
   }
 }
 
+// ------------------------------------------------------------------ fused pipelined PCG
+// Contact partition: block g owns contacts [g*chunk, (g+1)*chunk) (Morton order,
+// so a chunk is spatially compact) and gathers every body its contacts touch
+// into shared memory; bodies on chunk borders are gathered by each block that
+// needs them.  A matrix-vector product then needs no grid barrier.
+struct Part {
+  int chunk;
+  int maxb;
+  const int* nb;      // [G] bodies per block
+  const int* bodies;  // [G][maxb] global body ids
+  const int* cl;      // [2 Nc] local index of body a, body b (-1: static floor)
+};
+
+__global__ void k_partition(int Nc, int M, int chunk, int maxb, const int* __restrict__ ca,
+                            const int* __restrict__ cb, int* __restrict__ nb, int* __restrict__ bodies,
+                            int* __restrict__ cl) {
+  extern __shared__ int sb[];
+  const int g = blockIdx.x;
+  const int c0 = g * chunk, c1 = min(Nc, c0 + chunk);
+  const int nref = 2 * max(0, c1 - c0);
+  int n2 = 1;
+  while (n2 < nref) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    int v = 0x7fffffff;
+    if (i < nref) {
+      const int c = c0 + (i >> 1);
+      const int body = (i & 1) ? cb[c] : ca[c];
+      if (body < M) v = body;
+    }
+    sb[i] = v;
+  }
+  __syncthreads();
+  // bitonic sort
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const int a = sb[i], b = sb[l];
+          if ((a > b) == up) {
+            sb[i] = b;
+            sb[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // unique (serial compaction by thread 0: at most a few thousand entries)
+  __shared__ int cnt;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int i = 0; i < n2; ++i) {
+      const int v = sb[i];
+      if (v == 0x7fffffff) break;
+      if (k == 0 || sb[k - 1] != v) sb[k++] = v;
+    }
+    cnt = k;
+    nb[g] = k;
+  }
+  __syncthreads();
+  const int nbk = cnt;
+  for (int i = threadIdx.x; i < nbk; i += blockDim.x) bodies[(long long)g * maxb + i] = sb[i];
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    for (int side = 0; side < 2; ++side) {
+      const int body = side ? cb[c] : ca[c];
+      int idx = -1;
+      if (body < M) {
+        int lo = 0, hi = nbk - 1;
+        while (lo <= hi) {
+          const int mid = (lo + hi) >> 1;
+          const int v = sb[mid];
+          if (v == body) {
+            idx = mid;
+            break;
+          }
+          if (v < body) lo = mid + 1;
+          else hi = mid - 1;
+        }
+      }
+      cl[2 * c + side] = idx;
+    }
+  }
+}
+
+// Per-row records of the pipelined solver (8 values of type T each):
+//   pipe  record: w[2], n[2], z[2] (ping-pong pairs), M^-1 (Jacobi), 0
+//   state record: e, r, u, p, q, s, b, 0
+// One or two vector loads fetch everything a row needs.
+template <class T>
+__device__ __forceinline__ void load8(const T* p, T (&v)[8]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    float4 a = q[0], b = q[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = q[0], b = q[1], c = q[2], d = q[3];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+  }
+}
+template <class T>
+__device__ __forceinline__ void store8(T* p, const T (&v)[8]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* q = reinterpret_cast<float4*>(p);
+    q[0] = make_float4(v[0], v[1], v[2], v[3]);
+    q[1] = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(v[0], v[1]);
+    q[1] = make_double2(v[2], v[3]);
+    q[2] = make_double2(v[4], v[5]);
+    q[3] = make_double2(v[6], v[7]);
+  }
+}
+
+// operand M^-1 b for the first product (b from the state record)
+template <class T>
+struct OpRhs {
+  const T* pr;
+  const T* sr;
+  __device__ __forceinline__ T operator()(long long i) const { return pr[i * 8 + 6] * sr[i * 8 + 6]; }
+};
+// operand M^-1 w (w = w[slot] of the pipe record)
+template <class T>
+struct OpW {
+  const T* pr;
+  int slot;
+  __device__ __forceinline__ T operator()(long long i) const { return pr[i * 8 + 6] * pr[i * 8 + slot]; }
+};
+// operand M^-1 w_next, w_next = w[cur] - alpha (n[cur] + beta z[nxt]), all from one record load
+template <class T>
+struct OpPipe {
+  const T* pr;
+  int cur;
+  T alpha, beta;
+  __device__ __forceinline__ T operator()(long long i) const {
+    T v[8];
+    load8(pr + i * 8, v);
+    const T w = cur ? v[1] : v[0];
+    const T nn = cur ? v[3] : v[2];
+    const T z = cur ? v[4] : v[5];
+    return v[6] * (w - alpha * (nn + beta * z));
+  }
+};
+
+// Plain FP64 operand (outer residual).
+template <class T>
+struct PlainOp {
+  const T* x;
+  __device__ __forceinline__ T operator()(long long i) const { return x[i]; }
+};
+
+// y = S x for the rows of this block's contacts; x is evaluated through `op`;
+// row i of y is stored at y[i * ys].
+template <class T, class X>
+__device__ void fused_apply(const SysView<T>& s, const Part& pt, const X& op, T* y, int ys, T* wl) {
+  const int g = blockIdx.x;
+  const int nbk = pt.nb[g];
+  for (int lb = threadIdx.x; lb < nbk; lb += blockDim.x) {
+    const int b = pt.bodies[(long long)g * pt.maxb + lb];
+    T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
+    const int e = __ldg(s.bptr + b + 1);
+#pragma unroll 2
+    for (int k = __ldg(s.bptr + b); k < e; ++k) {
+      const int code = __ldg(s.inc + k);
+      const int c = code >> 1;
+      const long long row = (long long)s.slots * c;
+      T R[16];
+      load_rec(s.rec, c, R);
+      const T x0 = op(row), x1 = op(row + 1), x2 = op(row + 2);
+      T f0 = R[0] * x0 + R[3] * x1 + R[6] * x2;
+      T f1 = R[1] * x0 + R[4] * x1 + R[7] * x2;
+      T f2 = R[2] * x0 + R[5] * x1 + R[8] * x2;
+      const bool sb = (code & 1) != 0;
+      const T a0 = sb ? R[12] : R[9], a1 = sb ? R[13] : R[10], a2 = sb ? R[14] : R[11];
+      const T sg = sb ? T(1) : T(-1);
+      f0 *= sg;
+      f1 *= sg;
+      f2 *= sg;
+      F0 += f0;
+      F1 += f1;
+      F2 += f2;
+      Q0 += a1 * f2 - a2 * f1;
+      Q1 += a2 * f0 - a0 * f2;
+      Q2 += a0 * f1 - a1 * f0;
+    }
+    const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+    T* o = wl + (long long)lb * 8;
+    o[0] = im * F0;
+    o[1] = im * F1;
+    o[2] = im * F2;
+    o[3] = iI * Q0;
+    o[4] = iI * Q1;
+    o[5] = iI * Q2;
+  }
+  __syncthreads();
+  const int c0 = g * pt.chunk, c1 = min(s.Nc, c0 + pt.chunk);
+  const long long n = s.Nc;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    T R[16];
+    load_rec(s.rec, c, R);
+    const int la = pt.cl[2 * c], lb = pt.cl[2 * c + 1];
+    const T* wb = wl + (long long)lb * 8;
+    T d0 = wb[0] + (wb[4] * R[14] - wb[5] * R[13]);
+    T d1 = wb[1] + (wb[5] * R[12] - wb[3] * R[14]);
+    T d2 = wb[2] + (wb[3] * R[13] - wb[4] * R[12]);
+    if (la >= 0) {
+      const T* wa = wl + (long long)la * 8;
+      d0 -= wa[0] + (wa[4] * R[11] - wa[5] * R[10]);
+      d1 -= wa[1] + (wa[5] * R[9] - wa[3] * R[11]);
+      d2 -= wa[2] + (wa[3] * R[10] - wa[4] * R[9]);
+    }
+    const long long row = (long long)s.slots * c;
+    const T x0 = op(row), x1 = op(row + 1), x2 = op(row + 2);
+    T y0 = R[0] * d0 + R[1] * d1 + R[2] * d2;
+    T y1 = R[3] * d0 + R[4] * d1 + R[5] * d2;
+    T y2 = R[6] * d0 + R[7] * d1 + R[8] * d2;
+    if (s.H) {
+      const T* H = s.H;
+      T h00 = __ldg(H + c), h01 = __ldg(H + n + c), h02 = __ldg(H + 2 * n + c);
+      T h11 = __ldg(H + 3 * n + c), h12 = __ldg(H + 4 * n + c), h22 = __ldg(H + 5 * n + c);
+      y0 += h00 * x0 + h01 * x1 + h02 * x2;
+      y1 += h01 * x0 + h11 * x1 + h12 * x2;
+      y2 += h02 * x0 + h12 * x1 + h22 * x2;
+    }
+    y[row * ys] = y0;
+    y[(row + 1) * ys] = y1;
+    y[(row + 2) * ys] = y2;
+    if (s.slots == 4) y[(row + 3) * ys] = op(row + 3);
+  }
+  __syncthreads();
+}
+
+struct FusedArgs {
+  SysView<double> s64;
+  SysView<float> s32;
+  Part pt;
+  int nrow;
+  long long P;
+  const double* rhs;
+  double* x;
+  double* r64;
+  double* q64;
+  void* pool;          // 13 vectors of type T, P each
+  const void* dinv;
+  double tol, inner_tol;
+  int maxit, max_outer;
+  DevCtl* ctl;
+  double* partial;
+};
+
+template <class T>
+__device__ __forceinline__ const SysView<T>& fsys(const FusedArgs& a);
+template <>
+__device__ __forceinline__ const SysView<double>& fsys<double>(const FusedArgs& a) { return a.s64; }
+template <>
+__device__ __forceinline__ const SysView<float>& fsys<float>(const FusedArgs& a) { return a.s32; }
+
+// Sum of three consecutive partial slots over all blocks, in one pass.
+__device__ void grid_total3(const double* partial, int slot, double (&out)[3]) {
+  __shared__ double sm[3][NWMAX];
+  __shared__ double res[3];
+  double x[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int k = 0; k < 3; ++k) x[k] += *(volatile const double*)&partial[(size_t)b * NRED + slot + k];
+  for (int k = 0; k < 3; ++k) {
+    double v = warp_sum(x[k]);
+    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[threadIdx.x][w];
+    res[threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int k = 0; k < 3; ++k) out[k] = res[k];
+  __syncthreads();
+}
+
+// Pipelined Jacobi-PCG (Ghysels and Vanroose, Parallel Computing 40 (2014),
+// Alg. 3) on S_T e = b, x0 = 0, b in the state records.  One grid barrier per
+// iteration: it publishes the new n, w, z and completes the reduction of
+// (r,u), (w,u), (r,r).  Returns 0 converged, 1 cap, 2 breakdown, -1 barrier failure.
+template <class T>
+__device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& iters, T* wl) {
+  const SysView<T>& s = fsys<T>(A);
+  T* pool = static_cast<T*>(A.pool);
+  T* pr = pool;                  // pipe records   [P][8]
+  T* sr = pool + 8 * A.P;        // state records  [P][8]
+  const unsigned nb = gridDim.x;
+  const int g = blockIdx.x;
+  const int c0 = g * A.pt.chunk, c1 = min(s.Nc, c0 + A.pt.chunk);
+  const long long r0 = (long long)s.slots * c0, r1 = (long long)s.slots * c1;
+  // phase I: e = 0, r = b, u = M^-1 b, p = q = s = 0, z = 0; w0 = S u -> pipe n[1]
+  // (stored in the n slot of the other parity, moved to w[0] below)
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const T bi = sr[i * 8 + 6];
+    T pv[8];
+    load8(pr + i * 8, pv);
+    const T ui = pv[6] * bi;
+    const T ns[8] = {T(0), bi, ui, T(0), T(0), T(0), bi, T(0)};
+    store8(sr + i * 8, ns);
+    pr[i * 8 + 4] = T(0);
+    pr[i * 8 + 5] = T(0);
+    acc[0] += (double)bi * (double)ui;
+    acc[1] += (double)bi * (double)bi;
+  }
+  // w0 = S M^-1 b into the n[1] slot of each row (no one reads n[1] in this phase)
+  fused_apply(s, A.pt, OpRhs<T>{pr, sr}, pr + 3, 8, wl);
+  block_partials<3>(acc, A.partial, 0);
+  if (!grid_barrier(A.ctl, nb)) return -1;
+  double tot[3];
+  grid_total3(A.partial, 0, tot);
+  double gamma = tot[0];
+  const double bb = tot[1];
+  if (bb == 0.0) return 0;
+  // phase 0: w[0] <- n[1] (own rows); n0 = S M^-1 w0 into n[0]; delta0 = (w0, u0)
+  double acc1[3] = {0.0, 0.0, 0.0};
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const T w0 = pr[i * 8 + 3];
+    pr[i * 8 + 0] = w0;
+    acc1[0] += (double)w0 * (double)sr[i * 8 + 2];
+  }
+  __syncthreads();
+  // other blocks read w0 of our rows through n[1]: use that slot as the operand
+  fused_apply(s, A.pt, OpW<T>{pr, 3}, pr + 2, 8, wl);
+  block_partials<3>(acc1, A.partial, 3);
+  if (!grid_barrier(A.ctl, nb)) return -1;
+  grid_total3(A.partial, 3, tot);
+  double delta = tot[0];
+  if (!(gamma > 0.0) || !(delta > 0.0)) return 2;
+  double alpha = gamma / delta, beta = 0.0;
+  const double stop = tol * tol * bb;
+  int cur = 0;  // w[cur] = w_i, n[cur] = n_i, z[cur ^ 1] = z_{i-1}
+  for (int it = 0; it < maxit; ++it) {
+    const T a = (T)alpha, bt = (T)beta;
+    const int nxt = cur ^ 1;
+    double d3[3] = {0.0, 0.0, 0.0};
+#pragma unroll 2
+    for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      T pv[8], st[8];
+      load8(pr + i * 8, pv);
+      load8(sr + i * 8, st);
+      const T wi = cur ? pv[1] : pv[0];
+      const T ni = cur ? pv[3] : pv[2];
+      const T zp = cur ? pv[4] : pv[5];
+      const T mi = pv[6] * wi;
+      const T zi = ni + bt * zp;
+      const T qi = mi + bt * st[4];
+      const T si = wi + bt * st[5];
+      const T pi = st[2] + bt * st[3];
+      const T ei = st[0] + a * pi;
+      const T ri = st[1] - a * si;
+      const T ui = st[2] - a * qi;
+      const T wn = wi - a * zi;
+      pr[i * 8 + nxt] = wn;        // w[nxt]
+      pr[i * 8 + 4 + cur] = zi;    // z[cur]
+      const T ns[8] = {ei, ri, ui, pi, qi, si, st[6], T(0)};
+      store8(sr + i * 8, ns);
+      d3[0] += (double)ri * (double)ui;
+      d3[1] += (double)wn * (double)ui;
+      d3[2] += (double)ri * (double)ri;
+    }
+    // n_{i+1} = S M^-1 w_{i+1}, w_{i+1} formed on the fly from (w_i, n_i, z_{i-1})
+    fused_apply(s, A.pt, OpPipe<T>{pr, cur, a, bt}, pr + 2 + nxt, 8, wl);
+    // one barrier per iteration: alternate the partial-sum slots so that a block
+    // already in the next iteration never overwrites sums still being read
+    const int sl = 6 + 3 * (it & 1);
+    block_partials<3>(d3, A.partial, sl);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    ++iters;
+    grid_total3(A.partial, sl, tot);
+    const double gnew = tot[0], dnew = tot[1], rr = tot[2];
+    if (rr <= stop) return 0;
+    if (!(gnew > 0.0)) return 2;
+    beta = gnew / gamma;
+    const double den = dnew - beta * gnew / alpha;
+    if (!(den > 0.0)) return 2;
+    alpha = gnew / den;
+    gamma = gnew;
+    cur = nxt;
+  }
+  return 1;
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT_FUSED, 1) k_pcg_fused(FusedArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const unsigned nb = gridDim.x;
+  const SysView<double>& s64 = A.s64;
+  T* pool = static_cast<T*>(A.pool);
+  T* pr = pool;
+  T* sr = pool + 8 * A.P;
+  const T* dinv = static_cast<const T*>(A.dinv);
+  double a0[1] = {0.0};
+  for (long long i = tid; i < A.P; i += gsz) {
+    A.x[i] = 0.0;
+    if (i < A.nrow) {
+      a0[0] += A.rhs[i] * A.rhs[i];
+      pr[i * 8 + 6] = dinv[i];
+    }
+  }
+  block_partials<1>(a0, A.partial, 12);
+  if (!grid_barrier(A.ctl, nb)) return;
+  const double bnorm = sqrt(grid_total(A.partial, 12));
+  int iters = 0, status = 0, outer = 0;
+  double rel = 0.0;
+  const int g = blockIdx.x;
+  const int c0 = g * A.pt.chunk, c1 = min(s64.Nc, c0 + A.pt.chunk);
+  const long long r0 = (long long)s64.slots * c0, r1 = (long long)s64.slots * c1;
+  if (bnorm > 0.0) {
+    for (outer = 0;; ++outer) {
+      double rr[1] = {0.0};
+      if (outer == 0) {
+        for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+          A.r64[i] = A.rhs[i];
+          rr[0] += A.rhs[i] * A.rhs[i];
+        }
+      } else {
+        fused_apply(s64, A.pt, PlainOp<double>{A.x}, A.q64, 1, reinterpret_cast<double*>(smem_raw));
+        for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+          const double ri = A.rhs[i] - A.q64[i];
+          A.r64[i] = ri;
+          rr[0] += ri * ri;
+        }
+      }
+      block_partials<1>(rr, A.partial, 13);
+      if (!grid_barrier(A.ctl, nb)) return;
+      const double rn = sqrt(grid_total(A.partial, 13));
+      rel = rn / bnorm;
+      if (rel <= A.tol) {
+        status = 0;
+        break;
+      }
+      if (outer >= A.max_outer || iters >= A.maxit) {
+        status = 1;
+        break;
+      }
+      const double inv = 1.0 / rn;
+      for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) sr[i * 8 + 6] = (T)(A.r64[i] * inv);
+      if (!grid_barrier(A.ctl, nb)) return;
+      const int before = iters;
+      const int st = inner_pcg_fused<T>(A, A.inner_tol, A.maxit - iters, iters, reinterpret_cast<T*>(smem_raw));
+      if (st < 0) return;
+      for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.x[i] += rn * (double)sr[i * 8];
+      if (!grid_barrier(A.ctl, nb)) return;
+      // a pipelined-CG breakdown after some progress (loss of orthogonality near
+      // the attainable accuracy) restarts from the true residual; a breakdown
+      // without progress is reported
+      if (st == 2 && iters == before) {
+        status = 2;
+        break;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.ctl->iters = iters;
+    A.ctl->outer = outer;
+    A.ctl->scal[S_RELRES] = rel;
+    A.ctl->scal[S_BNORM] = bnorm;
+    A.ctl->halvings = status;
+  }
+}
+
 // Jacobi diagonal of S: diag(N) + diag(H); dummy rows 1.
 __global__ void k_diag(SysView<double> s, const double* __restrict__ H, double* __restrict__ d64,
                        float* __restrict__ d32, long long P) {
@@ -912,6 +1386,82 @@ static void pdip_pre(qp_ctx* c, qp_state* st, int mode, const qp_pdip_opts* o) {
   coop_launch2(c, k_pdip_pre, grid, A, mode);
 }
 
+// Build (or reuse) the contact partition for a grid of G blocks.
+static void ensure_partition(qp_ctx* c, int G) {
+  if (c->part_G == G) return;
+  const int Nc = c->Nc;
+  const int chunk = std::max(1, (Nc + G - 1) / G);
+  QP_REQUIRE(chunk <= 16384, QP_INVALID_ARG, "too many contacts per block for the fused Krylov kernel");
+  int n2 = 1;
+  while (n2 < 2 * chunk) n2 <<= 1;
+  const int maxb = 2 * chunk;
+  int* nb = static_cast<int*>(c->part_nb.ensure((size_t)G * sizeof(int)));
+  int* bodies = static_cast<int*>(c->part_bodies.ensure((size_t)G * maxb * sizeof(int)));
+  int* cl = static_cast<int*>(c->part_cl.ensure(2 * (size_t)std::max(Nc, 1) * sizeof(int)));
+  const size_t smem = (size_t)n2 * sizeof(int);
+  QP_CUDA(cudaFuncSetAttribute(k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_partition<<<G, 1024, smem, c->stream>>>(Nc, c->M, chunk, maxb, c->ca.as<int>(), c->cb.as<int>(), nb, bodies, cl);
+  QP_CUDA(cudaGetLastError());
+  std::vector<int> h(G);
+  QP_CUDA(cudaMemcpyAsync(h.data(), nb, (size_t)G * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  QP_CUDA(cudaStreamSynchronize(c->stream));
+  int mx = 1;
+  for (int v : h) mx = std::max(mx, v);
+  c->part_G = G;
+  c->part_chunk = chunk;
+  c->part_maxb = maxb;
+  c->part_nbmax = mx;
+}
+
+template <class T>
+static void launch_fused(qp_ctx* c, FusedArgs& A) {
+  auto k = k_pcg_fused<T>;
+  const size_t smem = (size_t)c->part_nbmax * 8 * sizeof(double);
+  QP_REQUIRE(smem <= 200 * 1024, QP_INVALID_ARG, "fused Krylov kernel: body set of a block exceeds shared memory");
+  QP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  QP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT_FUSED, smem));
+  QP_REQUIRE(per_sm >= 1, QP_CUDA_ERROR, "fused Krylov kernel does not fit on an SM");
+  const int G = c->part_G;
+  QP_REQUIRE(G <= per_sm * c->num_sms, QP_CUDA_ERROR, "fused Krylov grid exceeds co-resident blocks");
+  void* args[] = {&A};
+  QP_CUDA(cudaLaunchCooperativeKernel((const void*)k, dim3(G), dim3(NT_FUSED), args, smem, c->stream));
+}
+
+static void solve_fused(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o, bool mixed) {
+  // one block per SM: the partition is built for that grid
+  const int G = c->num_sms;
+  ensure_partition(c, G);
+  const size_t P = (size_t)c->P;
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  FusedArgs A;
+  A.s64 = view64(c, true);
+  A.s32 = view32(c, true);
+  A.pt.chunk = c->part_chunk;
+  A.pt.maxb = c->part_maxb;
+  A.pt.nb = c->part_nb.as<int>();
+  A.pt.bodies = c->part_bodies.as<int>();
+  A.pt.cl = c->part_cl.as<int>();
+  A.nrow = c->slots * c->Nc;
+  A.P = c->P;
+  A.rhs = rhs;
+  A.x = dx;
+  A.r64 = static_cast<double*>(c->v64[5].ensure(P * sizeof(double)));
+  A.q64 = static_cast<double*>(c->v64[6].ensure(P * sizeof(double)));
+  A.pool = (mixed ? c->v32[0] : c->scratch[0]).ensure(16 * P * es);  // pipe + state records
+  A.dinv = mixed ? (const void*)c->dinv32.p : (const void*)c->dinv.p;
+  A.tol = o->tol;
+  A.inner_tol = mixed ? (o->inner_tol > 0 ? o->inner_tol : 1e-4) : (o->inner_tol > 0 ? o->inner_tol : o->tol);
+  A.maxit = o->maxit;
+  A.max_outer = o->max_outer > 0 ? o->max_outer : (mixed ? 50 : 20);
+  A.ctl = c->ctl.as<DevCtl>();
+  A.partial = c->partial.as<double>();
+  reset_ctl(c);
+  QP_CUDA(cudaEventRecord(c->ev0, c->stream));
+  if (mixed) launch_fused<float>(c, A);
+  else launch_fused<double>(c, A);
+}
+
 // solve S dx = rhs with the current H blocks (already built for st)
 static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o) {
   ensure_partial(c);
@@ -972,19 +1522,39 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   k_diag<<<c->num_sms * 4, 256, 0, c->stream>>>(s64, c->H.as<double>(), c->dinv.as<double>(), c->dinv32.as<float>(),
                                                 c->P);
   QP_CUDA(cudaGetLastError());
-  reset_ctl(c);
-  QP_CUDA(cudaEventRecord(c->ev0, c->stream));
-  if (mixed) {
-    if (cdt == QP_BF16) {
-      auto k = k_pcg<float, __nv_bfloat16>;
-      coop_launch(c, k, coop_grid(c, k), A);
-    } else {
+  // Jacobi preconditioner: pipelined CG with the fused operator (one grid
+  // barrier per iteration) on small systems, classic CG otherwise; a failed
+  // pipelined solve (its recurrence residual can drift from the true one at
+  // tight FP64 tolerances) is redone with classic CG.
+  bool done = false;
+  // The fused kernel removes two of the three grid barriers of an iteration but
+  // gathers border bodies redundantly and forms its operand on the fly; that
+  // pays off while iterations are barrier-bound (few contacts per block).
+  const bool fused = !use_qtt && (c->Nc + c->num_sms - 1) / c->num_sms <= FUSED_MAX_CHUNK;
+  if (fused) {
+    solve_fused(c, rhs, dx, o, mixed);
+    QP_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    QP_CUDA(cudaStreamSynchronize(c->stream));
+    done = c->ctl_host->err == 0 && c->ctl_host->halvings == 0;
+  }
+  if (!done) {
+    reset_ctl(c);
+    QP_CUDA(cudaEventRecord(c->ev0, c->stream));
+    if (mixed && use_qtt) {
+      if (cdt == QP_BF16) {
+        auto k = k_pcg<float, __nv_bfloat16>;
+        coop_launch(c, k, coop_grid(c, k), A);
+      } else {
+        auto k = k_pcg<float, float>;
+        coop_launch(c, k, coop_grid(c, k), A);
+      }
+    } else if (mixed) {
       auto k = k_pcg<float, float>;
       coop_launch(c, k, coop_grid(c, k), A);
+    } else {
+      auto k = k_pcg<double, double>;
+      coop_launch(c, k, coop_grid(c, k), A);
     }
-  } else {
-    auto k = k_pcg<double, double>;
-    coop_launch(c, k, coop_grid(c, k), A);
   }
   QP_CUDA(cudaEventRecord(c->ev1, c->stream));
   DevCtl h = read_ctl(c);
