@@ -216,6 +216,70 @@ def run_ours(args):
     ach = sum(bytes_per) / (sum(pcg_ms) / 1e3) / 1e9
     peak, src = peaks()
 
+    # QTT leg (Sec. 3.3): the same PDIP iterates solved with the QTT-preconditioned
+    # PCG, the preconditioner refreshed (compressed + inverted, warm-started) each step
+    qtt_out = None
+    if not qtt and args.qtt_steps > 0:
+        g_save, l_save = gamma.clone(), lam.clone()
+        ctxq = binding.Context()
+        workload.assemble(ctxq, scene)
+        gq, lq = gamma.clone(), lam.clone()
+        stq = ctxq.state(gq, lq)
+        soq = ctxq.solve_opts(binding.QP_QTT_PCG, None, tol=1e-8, maxit=200000, mixed=mixed,
+                              inner_tol=1e-3 if mixed else 0.0, max_outer=60,
+                              core_dtype=binding.QP_BF16 if mixed else binding.QP_F32)
+        optq = ctxq.pdip_opts(soq, qtt_refresh=1, qtt_eps=args.qtt_eps, qtt_rmax=args.qtt_rmax)
+        q_ms, q_it, q_ref, q_solve = [], [], [], []
+        for _ in range(args.qtt_steps):
+            gq.copy_(g_save)
+            lq.copy_(l_save)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sq = ctxq.pdip_step(stq, optq, allow=(binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL))
+            e1.record(stream)
+            e1.synchronize()
+            q_ms.append(e0.elapsed_time(e1))
+            q_it.append(sq.solve.iters)
+            q_ref.append(sq.ms_refresh)
+            q_solve.append(sq.solve.ms)
+        # standalone QTT apply of the refreshed preconditioner (FP32 vectors, BF16 or FP32 cores)
+        S_tt = ctxq.qtt_compress(stq, args.qtt_eps, args.qtt_rmax)
+        X = ctxq.qtt_inverse(S_tt, args.qtt_eps, args.qtt_rmax, sweeps=2)
+        ranks = X.ranks()
+        xin = torch.randn(P, dtype=torch.float32, device=dev)
+        yout = torch.empty_like(xin)
+        cdt = binding.QP_BF16 if mixed else binding.QP_F32
+        for _ in range(3):
+            ctxq.qtt_apply(X, xin, yout, cdt, binding.QP_F32)
+        ap_ms = []
+        for _ in range(10):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctxq.qtt_apply(X, xin, yout, cdt, binding.QP_F32)
+            e1.record(stream)
+            e1.synchronize()
+            ap_ms.append(e0.elapsed_time(e1))
+        # unfused schedule: step k reads r_k * N and writes r_{k-1} * N FP32 values
+        ap_bytes = sum((ranks[k] + ranks[k + 1]) * P * 4 for k in range(len(ranks) - 1))
+        ap_flops = sum(4 * ranks[k] * ranks[k + 1] * P for k in range(len(ranks) - 1))
+        ap_t = statistics.median(ap_ms) / 1e3
+        qv = 1e3 / statistics.mean(q_ms)
+        qtt_out = {"value": qv, "unit": UNIT, "factor_vs_jacobi": qv / value,
+                   "solve_only_factor_vs_jacobi": statistics.mean(step_ms) / statistics.mean(q_solve),
+                   "krylov_iters_per_solve": statistics.mean(q_it), "refresh_ms": statistics.mean(q_ref),
+                   "solve_ms": statistics.mean(q_solve), "eps": args.qtt_eps, "rmax": args.qtt_rmax,
+                   "inverse_ranks_max": max(ranks),
+                   "qtt_apply": {"us": ap_t * 1e6, "bound": "hbm", "achieved": ap_bytes / ap_t / 1e9,
+                                 "peak": peaks()[0], "unit": "GB/s", "frac": ap_bytes / ap_t / 1e9 / peaks()[0],
+                                 "tflops": ap_flops / ap_t / 1e12, "schedule": "one core per launch, unfused"}}
+        for h in (X, S_tt):
+            h.free()
+        ctxq.close()
+
     # end to end through the C ABI with host buffers: H2D scene + state, assemble, step, D2H state
     host = {k: v.cpu().pin_memory() for k, v in workload.scene_to_device(scene, dev).items()}
     g_h = gamma.cpu().pin_memory()
@@ -260,6 +324,7 @@ def run_ours(args):
         "qtt_refresh_ms_per_step": statistics.mean(refresh_ms) if qtt else None,
         "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "hbm", "achieved": ach, "peak": peak,
                      "unit": "GB/s", "frac": ach / peak, "peak_source": src, "traffic": None},
+        "qtt_pcg": qtt_out,
         "e2e": {"value": 1e3 / e2e_ms_max * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
@@ -371,6 +436,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=1000)
     ap.add_argument("--qtt-eps", type=float, default=1e-2)
     ap.add_argument("--qtt-rmax", type=int, default=10)
+    ap.add_argument("--qtt-steps", type=int, default=1, help="PDIP steps of the QTT-PCG comparison leg (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

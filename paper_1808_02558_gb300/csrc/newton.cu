@@ -390,7 +390,7 @@ __device__ bool qtt_precond(const PcgArgs& A, const T* r, T* z) {
   for (int k = q.d; k >= 1; --k) {
     T* out = (k == 1) ? z : static_cast<T*>(((q.d - k) & 1) ? A.qw1 : A.qw0);
     for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items; it += gsz)
-      qtt_step_item<T, T, TC>(q, k, in, out, it);
+      qtt_step_any<T, T, TC>(q, k, in, out, it);
     if (!grid_barrier(A.ctl, gridDim.x)) return false;
     in = out;
   }

@@ -12,7 +12,7 @@ template <class TV, class TA, class TC>
 __global__ void k_qtt_step(QttDev q, int k, const TV* in, TV* out, long long items) {
   const long long gsz = (long long)gridDim.x * blockDim.x;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items; it += gsz)
-    qtt_step_item<TV, TA, TC>(q, k, in, out, it);
+    qtt_step_any<TV, TA, TC>(q, k, in, out, it);
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {

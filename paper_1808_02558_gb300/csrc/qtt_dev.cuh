@@ -72,4 +72,62 @@ __device__ __forceinline__ void qtt_step_item(const QttDev& q, int k, const TV* 
   }
 }
 
+// Same step with the 2 r_k inputs of the column held in registers (r_k <= R):
+// each input is loaded once, each core value once per output row.
+template <int R, class TV, class TA, class TC>
+__device__ __forceinline__ void qtt_step_item_reg(const QttDev& q, int k, const TV* in, TV* out, long long item) {
+  const int d = q.d;
+  const int r0 = q.ranks[k - 1], r1 = q.ranks[k];
+  const int lowbits = d - k;
+  const long long nI = 1LL << lowbits;
+  const long long I = item & (nI - 1);
+  const long long Jp = item >> lowbits;
+  const TC* G = static_cast<const TC*>(q.cores) + q.off[k - 1];
+  const TV* in0 = in + ((2 * Jp) * r1) * nI + I;
+  const TV* in1 = in + ((2 * Jp + 1) * r1) * nI + I;
+  TA v0[R], v1[R];
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    v0[b] = b < r1 ? (TA)in0[(long long)b * nI] : TA(0);
+    v1[b] = b < r1 ? (TA)in1[(long long)b * nI] : TA(0);
+  }
+  TV* o = out + (Jp * r0) * (2 * nI) + I;
+  for (int a = 0; a < r0; ++a) {
+    const TC* Ga = G + (long long)a * 4 * r1;
+    TA acc0 = 0, acc1 = 0;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      if (b < r1) {
+        TA g00, g01, g10, g11;
+        if constexpr (sizeof(TC) == 8) {
+          g00 = (TA)__ldg(Ga + b);
+          g01 = (TA)__ldg(Ga + r1 + b);
+          g10 = (TA)__ldg(Ga + 2 * r1 + b);
+          g11 = (TA)__ldg(Ga + 3 * r1 + b);
+        } else {
+          g00 = (TA)core_f<TC>(Ga, b);
+          g01 = (TA)core_f<TC>(Ga, r1 + b);
+          g10 = (TA)core_f<TC>(Ga, 2 * r1 + b);
+          g11 = (TA)core_f<TC>(Ga, 3 * r1 + b);
+        }
+        acc0 += g00 * v0[b] + g01 * v1[b];
+        acc1 += g10 * v0[b] + g11 * v1[b];
+      }
+    }
+    o[(long long)a * 2 * nI] = (TV)acc0;
+    o[(long long)a * 2 * nI + nI] = (TV)acc1;
+  }
+}
+
+// Dispatch on the input rank of core k.
+template <class TV, class TA, class TC>
+__device__ __forceinline__ void qtt_step_any(const QttDev& q, int k, const TV* in, TV* out, long long item) {
+  const int r1 = q.ranks[k];
+  if (r1 <= 4) qtt_step_item_reg<4, TV, TA, TC>(q, k, in, out, item);
+  else if (r1 <= 8) qtt_step_item_reg<8, TV, TA, TC>(q, k, in, out, item);
+  else if (r1 <= 16) qtt_step_item_reg<16, TV, TA, TC>(q, k, in, out, item);
+  else if (r1 <= 32) qtt_step_item_reg<32, TV, TA, TC>(q, k, in, out, item);
+  else qtt_step_item<TV, TA, TC>(q, k, in, out, item);
+}
+
 }  // namespace qp

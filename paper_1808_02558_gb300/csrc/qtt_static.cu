@@ -47,7 +47,7 @@ int noalloc_scratch(float** out) {
 __global__ void k_qtt_step_noalloc(QttDev q, int k, const float* in, float* out, long long items) {
   const long long gsz = (long long)gridDim.x * blockDim.x;
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items; it += gsz)
-    qtt_step_item<float, float, float>(q, k, in, out, it);
+    qtt_step_any<float, float, float>(q, k, in, out, it);
 }
 
 }  // namespace
