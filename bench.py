@@ -121,26 +121,37 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def _reduce(v, world, op):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    device = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(v, world):
+    """Slowest rank's time: the job finishes when the last replica does."""
+    import torch.distributed as dist
+
+    return _reduce(v, world, dist.ReduceOp.MAX) if world > 1 else v
 
 
 def sum_over_ranks(v, world):
-    if world == 1:
-        return v
-    import torch
+    """Work done by all replicas together."""
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(v, world, dist.ReduceOp.SUM) if world > 1 else v
+
+
+def job_throughput(local_units, local_ms, world):
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    total = sum_over_ranks(local_units, world)
+    ms = max_over_ranks(local_ms, world)
+    return total / (ms / 1e3), ms
 
 
 # ---------------------------------------------------------------------- our arm
@@ -206,9 +217,7 @@ def run_ours(args):
                 launches += 2 * con.L + 40  # compression levels, inverse, rounding (approximate)
         torch.cuda.synchronize()
         barrier(world)
-    total_ms = max_over_ranks(sum(step_ms), world)
-    solves = sum_over_ranks(float(args.steps), world)
-    value = solves / (total_ms / 1e3)
+    value, total_ms = job_throughput(float(args.steps), sum(step_ms), world)
 
     # roofline of the dominant kernel (persistent PCG)
     nrow = 3 * Nc
