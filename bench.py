@@ -196,6 +196,7 @@ def run_ours(args):
     step_ms, pcg_ms, iters, outer, relres, refresh_ms = [], [], [], [], [], []
     launches = 0
     with ClockSampler(local) as clk:
+        time.sleep(0.5)  # let the sampler start before the timed region
         torch.cuda.synchronize()
         barrier(world)
         for _ in range(args.steps):
@@ -234,11 +235,12 @@ def run_ours(args):
         workload.assemble(ctxq, scene)
         gq, lq = gamma.clone(), lam.clone()
         stq = ctxq.state(gq, lq)
-        soq = ctxq.solve_opts(binding.QP_QTT_PCG, None, tol=1e-8, maxit=200000, mixed=mixed,
+        soq = ctxq.solve_opts(binding.QP_QTT_PCG, None, tol=1e-8, maxit=args.qtt_maxit, mixed=mixed,
                               inner_tol=1e-3 if mixed else 0.0, max_outer=60,
-                              core_dtype=binding.QP_BF16 if mixed else binding.QP_F32)
+                              core_dtype=binding.QP_BF16 if mixed else binding.QP_F32,
+                              krylov=binding.QP_BICGSTAB if args.qtt_krylov == "bicgstab" else binding.QP_CG)
         optq = ctxq.pdip_opts(soq, qtt_refresh=1, qtt_eps=args.qtt_eps, qtt_rmax=args.qtt_rmax)
-        q_ms, q_it, q_ref, q_solve = [], [], [], []
+        q_ms, q_it, q_ref, q_solve, q_fb = [], [], [], [], 0
         for _ in range(args.qtt_steps):
             gq.copy_(g_save)
             lq.copy_(l_save)
@@ -253,6 +255,7 @@ def run_ours(args):
             q_it.append(sq.solve.iters)
             q_ref.append(sq.ms_refresh)
             q_solve.append(sq.solve.ms)
+            q_fb += sq.solve.fallback
         # standalone QTT apply of the refreshed preconditioner (FP32 vectors, BF16 or FP32 cores)
         S_tt = ctxq.qtt_compress(stq, args.qtt_eps, args.qtt_rmax)
         X = ctxq.qtt_inverse(S_tt, args.qtt_eps, args.qtt_rmax, sweeps=2)
@@ -281,6 +284,7 @@ def run_ours(args):
                    "solve_only_factor_vs_jacobi": statistics.mean(step_ms) / statistics.mean(q_solve),
                    "krylov_iters_per_solve": statistics.mean(q_it), "refresh_ms": statistics.mean(q_ref),
                    "solve_ms": statistics.mean(q_solve), "eps": args.qtt_eps, "rmax": args.qtt_rmax,
+                   "krylov": args.qtt_krylov, "maxit": args.qtt_maxit, "jacobi_fallbacks": q_fb,
                    "inverse_ranks_max": max(ranks),
                    "qtt_apply": {"us": ap_t * 1e6, "bound": "hbm", "achieved": ap_bytes / ap_t / 1e9,
                                  "peak": peaks()[0], "unit": "GB/s", "frac": ap_bytes / ap_t / 1e9 / peaks()[0],
@@ -436,7 +440,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "qtt"])
@@ -446,6 +450,10 @@ def main():
     ap.add_argument("--qtt-eps", type=float, default=1e-2)
     ap.add_argument("--qtt-rmax", type=int, default=10)
     ap.add_argument("--qtt-steps", type=int, default=1, help="PDIP steps of the QTT-PCG comparison leg (0: skip)")
+    ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],
+                    help="Krylov method of the QTT leg (the paper uses BiCGSTAB)")
+    ap.add_argument("--qtt-maxit", type=int, default=5000,
+                    help="iteration cap of the QTT leg before the Jacobi fallback")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

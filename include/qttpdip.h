@@ -126,6 +126,7 @@ int newton_apply(qp_ctx_t ctx, const qp_state* st, const void* x, void* y, qp_dt
 int newton_rhs(qp_ctx_t ctx, const qp_state* st, double* rhs);
 
 typedef enum { QP_JACOBI_PCG = 0, QP_QTT_PCG = 1 } qp_precond;
+typedef enum { QP_CG = 0, QP_BICGSTAB = 1 } qp_krylov;
 
 typedef struct {
   qp_precond precond; /* Jacobi (diag S) or the QTT approximate inverse        */
@@ -136,6 +137,9 @@ typedef struct {
   double inner_tol;   /* mixed: relative tolerance of each inner solve         */
   int max_outer;      /* mixed: refinement cap                                 */
   qp_dtype core_dtype;/* QTT preconditioner core type (QP_F32 or QP_BF16)      */
+  qp_krylov krylov;   /* QP_CG (preconditioned CG) or QP_BICGSTAB (the Krylov
+                         method of the paper's Sec. 4.2, right-preconditioned;
+                         tolerates a nonsymmetric or indefinite preconditioner)  */
 } qp_solve_opts;
 
 typedef struct {
@@ -144,11 +148,14 @@ typedef struct {
   int outer;          /* refinement steps (mixed)                              */
   double rel_res;     /* true ||rhs - S dx|| / ||rhs|| in FP64                 */
   double ms;          /* device time of the solve                              */
+  int fallback;       /* 1: the QTT-preconditioned solve broke down and the
+                         system was solved again with the Jacobi preconditioner */
 } qp_solve_stats;
 
-/* Solve S dx = rhs (S at st) by preconditioned CG, run as one persistent
- * cooperative kernel (the whole Krylov loop stays on the device).  rhs, dx:
- * double[P].  stats may be NULL.                                            */
+/* Solve S dx = rhs (S at st) by preconditioned CG or BiCGSTAB, run as one
+ * persistent cooperative kernel (the whole Krylov loop stays on the device).
+ * rhs, dx: double[P].  stats may be NULL.  A breakdown of the QTT-preconditioned
+ * solve is followed by a Jacobi-preconditioned solve (stats->fallback = 1).   */
 int newton_solve(qp_ctx_t ctx, const qp_state* st, const double* rhs, double* dx,
                  const qp_solve_opts* opts, qp_solve_stats* stats);
 

@@ -20,6 +20,7 @@ QP_OK, QP_INVALID_ARG, QP_OOM, QP_CUDA_ERROR = 0, -1, -2, -3
 QP_NOT_CONVERGED, QP_BREAKDOWN, QP_LINESEARCH_FAIL, QP_TIMEOUT, QP_NOT_READY = -4, -5, -6, -7, -8
 QP_F64, QP_F32, QP_BF16 = 0, 1, 2
 QP_JACOBI_PCG, QP_QTT_PCG = 0, 1
+QP_CG, QP_BICGSTAB = 0, 1
 QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
@@ -48,12 +49,13 @@ class State(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("precond", C.c_int), ("X", C.c_void_p), ("tol", C.c_double), ("maxit", C.c_int),
-                ("mixed", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int), ("core_dtype", C.c_int)]
+                ("mixed", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int), ("core_dtype", C.c_int),
+                ("krylov", C.c_int)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("outer", C.c_int), ("rel_res", C.c_double),
-                ("ms", C.c_double)]
+                ("ms", C.c_double), ("fallback", C.c_int)]
 
 
 class PdipOpts(C.Structure):
@@ -243,9 +245,9 @@ class Context:
 
     @staticmethod
     def solve_opts(precond=QP_JACOBI_PCG, X=None, tol=1e-10, maxit=20000, mixed=0, inner_tol=0.0, max_outer=0,
-                   core_dtype=QP_F32) -> SolveOpts:
+                   core_dtype=QP_F32, krylov=QP_CG) -> SolveOpts:
         return SolveOpts(precond, X.h.value if X is not None else None, tol, maxit, mixed, inner_tol, max_outer,
-                         core_dtype)
+                         core_dtype, krylov)
 
     def newton_solve(self, st, rhs, dx, opts: SolveOpts, allow=(QP_NOT_CONVERGED, QP_BREAKDOWN)) -> SolveStats:
         stats = SolveStats()

@@ -367,6 +367,8 @@ struct PcgArgs {
   QttDev qtt;
   void* qw0;                // QTT work buffers (type T), rmax * P each
   void* qw1;
+  void* xb;                 // BiCGSTAB vectors (type T), 5 * P
+  int krylov;               // QP_CG or QP_BICGSTAB
   double tol, inner_tol;
   int maxit, max_outer;
   DevCtl* ctl;
@@ -501,6 +503,125 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   return 1;
 }
 
+// y = S x for the operator of precision T (two grid-synchronised phases).
+template <class T>
+__device__ bool op_apply(const PcgArgs& A, const SysView<T>& s, const T* x, T* y) {
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (int bd = (int)tid; bd < s.M; bd += (int)gsz) body_gather(s, plain(x), bd);
+  if (!grid_barrier(A.ctl, gridDim.x)) return false;
+  for (int c = (int)tid; c < s.Nc; c += (int)gsz) contact_apply(s, plain(x), y, c);
+  return grid_barrier(A.ctl, gridDim.x);
+}
+
+// out = M^-1 in: Jacobi or the QTT approximate inverse.
+template <class T, class TC>
+__device__ bool prec_apply(const PcgArgs& A, const T* in, T* out) {
+  if (A.use_qtt) return qtt_precond<T, TC>(A, in, out);
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const T* dinv = static_cast<const T*>(A.dinv);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.nrow; i += gsz) out[i] = dinv[i] * in[i];
+  return grid_barrier(A.ctl, gridDim.x);
+}
+
+// Right-preconditioned BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13
+// (1992)) on S_T e = b, e0 = 0: the Krylov method of the paper's Sec. 4.2.
+// Returns 0 converged, 1 cap, 2 breakdown, -1 barrier failure.
+template <class T, class TC>
+__device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iters) {
+  const SysView<T>& s = sys_of<T>(A);
+  const long long P = A.P;
+  T* b = static_cast<T*>(A.b);
+  T* x = static_cast<T*>(A.e);
+  T* r = static_cast<T*>(A.r);
+  T* p = static_cast<T*>(A.p);
+  T* z = static_cast<T*>(A.z);
+  T* xb = static_cast<T*>(A.xb);
+  T* rh = xb;
+  T* v = xb + P;
+  T* y = xb + 2 * P;
+  T* sv = xb + 3 * P;
+  T* t = xb + 4 * P;
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nrow = A.nrow;
+  const unsigned nb = gridDim.x;
+  double a0[1] = {0.0};
+  for (long long i = tid; i < P; i += gsz) {
+    if (i < nrow) {
+      const T bi = b[i];
+      x[i] = 0;
+      r[i] = bi;
+      rh[i] = bi;
+      v[i] = 0;
+      a0[0] += (double)bi * (double)bi;
+    }
+    p[i] = 0;   // the QTT preconditioner reads whole padded vectors
+    sv[i] = 0;
+  }
+  block_partials<1>(a0, A.partial, 8);
+  if (!grid_barrier(A.ctl, nb)) return -1;
+  const double bb = grid_total(A.partial, 8);
+  if (bb == 0.0) return 0;
+  const double stop = tol * tol * bb;
+  double rho = 1.0, alpha = 1.0, omega = 1.0, rho1 = bb;
+  for (int it = 0; it < maxit; ++it) {
+    if (rho1 == 0.0 || omega == 0.0) return 2;
+    const double beta = (rho1 / rho) * (alpha / omega);
+    rho = rho1;
+    for (long long i = tid; i < nrow; i += gsz) p[i] = r[i] + (T)beta * (p[i] - (T)omega * v[i]);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    if (!prec_apply<T, TC>(A, p, y)) return -1;
+    if (!op_apply<T>(A, s, y, v)) return -1;
+    double a1[1] = {0.0};
+    for (long long i = tid; i < nrow; i += gsz) a1[0] += (double)rh[i] * (double)v[i];
+    block_partials<1>(a1, A.partial, 9);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    const double rv = grid_total(A.partial, 9);
+    if (rv == 0.0) return 2;
+    alpha = rho / rv;
+    double a2[1] = {0.0};
+    for (long long i = tid; i < nrow; i += gsz) {
+      x[i] += (T)alpha * y[i];
+      const T si = r[i] - (T)alpha * v[i];
+      sv[i] = si;
+      a2[0] += (double)si * (double)si;
+    }
+    block_partials<1>(a2, A.partial, 10);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    if (grid_total(A.partial, 10) <= stop) {
+      ++iters;
+      return 0;
+    }
+    if (!prec_apply<T, TC>(A, sv, z)) return -1;
+    if (!op_apply<T>(A, s, z, t)) return -1;
+    double a3[2] = {0.0, 0.0};
+    for (long long i = tid; i < nrow; i += gsz) {
+      a3[0] += (double)t[i] * (double)sv[i];
+      a3[1] += (double)t[i] * (double)t[i];
+    }
+    block_partials<2>(a3, A.partial, 11);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    const double ts = grid_total(A.partial, 11), tt = grid_total(A.partial, 12);
+    if (!(tt > 0.0)) return 2;
+    omega = ts / tt;
+    double a4[2] = {0.0, 0.0};
+    for (long long i = tid; i < nrow; i += gsz) {
+      x[i] += (T)omega * z[i];
+      const T ri = sv[i] - (T)omega * t[i];
+      r[i] = ri;
+      a4[0] += (double)rh[i] * (double)ri;
+      a4[1] += (double)ri * (double)ri;
+    }
+    block_partials<2>(a4, A.partial, 13);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    ++iters;
+    rho1 = grid_total(A.partial, 13);
+    if (grid_total(A.partial, 14) <= stop) return 0;
+  }
+  return 1;
+}
+
 // FP64 outer refinement: r64 = rhs - S x; inner solve on r64/||r64||; x += ...
 template <class T, class TC>
 __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
@@ -562,7 +683,8 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
       const double inv = 1.0 / rn;
       for (long long i = tid; i < A.nrow; i += gsz) b[i] = (T)(A.r64[i] * inv);
       if (!grid_barrier(A.ctl, nb)) return;
-      int st = inner_pcg<T, TC>(A, A.inner_tol, A.maxit - iters, iters);
+      int st = A.krylov == QP_BICGSTAB ? inner_bicgstab<T, TC>(A, A.inner_tol, A.maxit - iters, iters)
+                                       : inner_pcg<T, TC>(A, A.inner_tol, A.maxit - iters, iters);
       if (st < 0) return;
       for (long long i = tid; i < A.nrow; i += gsz) A.x[i] += rn * (double)e[i];
       if (!grid_barrier(A.ctl, nb)) return;
@@ -1463,7 +1585,7 @@ static void solve_fused(qp_ctx* c, const double* rhs, double* dx, const qp_solve
 }
 
 // solve S dx = rhs with the current H blocks (already built for st)
-static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o) {
+static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o) {
   ensure_partial(c);
   QP_REQUIRE(o, QP_INVALID_ARG, "newton_solve: null options");
   QP_REQUIRE(o->tol > 0 && o->maxit > 0, QP_INVALID_ARG, "newton_solve: tol > 0 and maxit > 0 required");
@@ -1491,6 +1613,8 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   A.dinv = mixed ? (const void*)c->dinv32.p : (const void*)c->dinv.p;
   A.use_qtt = use_qtt ? 1 : 0;
   A.qw0 = A.qw1 = nullptr;
+  A.krylov = o->krylov == QP_BICGSTAB ? QP_BICGSTAB : QP_CG;
+  A.xb = A.krylov == QP_BICGSTAB ? c->dm[12].ensure(5 * P * es) : nullptr;
   qp_dtype cdt = QP_F64;
   if (use_qtt) {
     qp_qtt* X = o->X;
@@ -1530,7 +1654,7 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   // The fused kernel removes two of the three grid barriers of an iteration but
   // gathers border bodies redundantly and forms its operand on the fly; that
   // pays off while iterations are barrier-bound (few contacts per block).
-  const bool fused = !use_qtt && (c->Nc + c->num_sms - 1) / c->num_sms <= FUSED_MAX_CHUNK;
+  const bool fused = !use_qtt && A.krylov == QP_CG && (c->Nc + c->num_sms - 1) / c->num_sms <= FUSED_MAX_CHUNK;
   if (fused) {
     solve_fused(c, rhs, dx, o, mixed);
     QP_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
@@ -1569,7 +1693,25 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   else if (h.halvings == 2) out.status = QP_BREAKDOWN;
   else if (h.halvings == 1) out.status = QP_NOT_CONVERGED;
   else out.status = QP_OK;
+  out.fallback = 0;
   return out;
+}
+
+// A QTT-preconditioned solve that breaks down (the rank-truncated inverse need
+// not be definite) is redone with the Jacobi preconditioner on the device.
+static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o) {
+  qp_solve_stats st = solve_once(c, rhs, dx, o);
+  if (o->precond == QP_QTT_PCG && (st.status == QP_BREAKDOWN || st.status == QP_NOT_CONVERGED)) {
+    qp_solve_opts j = *o;
+    j.precond = QP_JACOBI_PCG;
+    j.X = nullptr;
+    qp_solve_stats s2 = solve_once(c, rhs, dx, &j);
+    s2.iters += st.iters;
+    s2.ms += st.ms;
+    s2.fallback = 1;
+    return s2;
+  }
+  return st;
 }
 
 }  // namespace qp

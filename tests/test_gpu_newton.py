@@ -156,3 +156,43 @@ def test_solve_qtt_preconditioned(pile8, mixed):
                                  pile8.ctx.solve_opts(tol=1e-10, maxit=20000, mixed=mixed,
                                                       inner_tol=1e-3 if mixed else 0.0, max_outer=60), allow=())
     print(f"QTT-PCG iters {stats.iters} vs Jacobi-PCG {jac.iters} (mixed={mixed})")
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_solve_bicgstab_jacobi_and_qtt(pile8, mixed):
+    """BiCGSTAB (the paper's Sec. 4.2 Krylov method), Jacobi and QTT preconditioned."""
+    g, lam = pile8.iters[3]
+    gd, ld, st = pile8.state(g, lam)
+    rhs = torch.empty(pile8.P, dtype=torch.float64, device="cuda")
+    pile8.ctx.newton_rhs(st, rhs)
+    S = qp.schur_matrix(pile8.N, g, lam, pile8.scene.mu)
+    b = pile8.unpad(to_np(rhs))
+    X = pile8.ctx.qtt_inverse(pile8.ctx.qtt_compress(st, 1e-2, 10), 1e-2, 10, sweeps=3)
+    for precond, Xh in ((binding.QP_JACOBI_PCG, None), (binding.QP_QTT_PCG, X)):
+        dx = torch.empty_like(rhs)
+        opts = pile8.ctx.solve_opts(precond, Xh, tol=1e-10, maxit=50000, mixed=mixed,
+                                    inner_tol=1e-3 if mixed else 0.0, max_outer=80,
+                                    core_dtype=binding.QP_BF16 if mixed else binding.QP_F32,
+                                    krylov=binding.QP_BICGSTAB)
+        stats = pile8.ctx.newton_solve(st, rhs, dx, opts, allow=())
+        res = np.linalg.norm(b - S @ pile8.unpad(to_np(dx))) / np.linalg.norm(b)
+        assert res <= 1.05e-10 and stats.rel_res <= 1e-10
+        if not mixed:
+            exact = sla.cho_solve(sla.cho_factor(S.toarray()), b)
+            assert relerr(pile8.unpad(to_np(dx)), exact) <= 1e-7
+
+
+def test_qtt_breakdown_falls_back_to_jacobi(pile8):
+    """An indefinite QTT preconditioner (X = -I) breaks CG down; the solve is redone with Jacobi."""
+    g, lam = pile8.iters[3]
+    gd, ld, st = pile8.state(g, lam)
+    rhs = torch.empty(pile8.P, dtype=torch.float64, device="cuda")
+    pile8.ctx.newton_rhs(st, rhs)
+    d = pile8.L
+    eye = [np.array([1.0, 0.0, 0.0, 1.0]).reshape(1, 4, 1) for _ in range(d)]
+    eye[0] = -eye[0]
+    Xneg = pile8.ctx.qtt_from_cores(eye)
+    dx = torch.empty_like(rhs)
+    stats = pile8.ctx.newton_solve(st, rhs, dx, pile8.ctx.solve_opts(binding.QP_QTT_PCG, Xneg, tol=1e-10,
+                                                                      maxit=50000), allow=())
+    assert stats.fallback == 1 and stats.status == binding.QP_OK and stats.rel_res <= 1e-10
