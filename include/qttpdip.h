@@ -166,9 +166,11 @@ typedef struct {
   double step_frac;   /* fraction of the max dual step              (0.99)     */
   int max_halvings;   /* backtracking cap                           (60)       */
   qp_solve_opts solve;/* Newton solve options                                  */
-  int qtt_refresh;    /* 1: compress S and invert it before the solve; the new
-                         inverse is kept by the context and warm-starts the
-                         next refresh (solve.X, when set, is the warm start)   */
+  int qtt_refresh;    /* 1: compress the Jacobi-scaled S~ = D^-1/2 S D^-1/2
+                         (D = diag S) and invert it before the solve; the
+                         preconditioner is D^-1/2 X~ D^-1/2.  The new inverse
+                         is kept by the context and warm-starts the next
+                         refresh (solve.X, when set, is the warm start)        */
   double qtt_eps;     /* TT accuracy of the refresh                            */
   int qtt_rmax;       /* TT rank cap of the refresh                            */
 } qp_pdip_opts;

@@ -69,6 +69,7 @@ struct qp_qtt {
   double* cores = nullptr;         // FP64 master copy (device)
   float* cores32 = nullptr;        // FP32 apply copy (device, lazily made)
   __nv_bfloat16* cores16 = nullptr;// BF16 apply copy (device, lazily made)
+  int scaled = 0;                  // 1: approximates D^-1/2 S D^-1/2 (or its inverse), D = diag(S)
 };
 
 struct qp_ctx {
@@ -140,5 +141,7 @@ void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype cor
 void qtt_prepare_copies(qp_ctx* c, qp_qtt* A, qp_dtype core_dt);
 qp_qtt* qtt_alloc(qp_ctx* c, int d, const std::vector<int>& ranks);
 size_t qtt_work_bytes(qp_qtt* A, qp_dtype core_dt);
+qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax, const double* rowscale);
+void launch_rowscale(qp_ctx* c, double* rowscale);
 
 }  // namespace qp

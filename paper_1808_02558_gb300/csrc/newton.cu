@@ -203,34 +203,42 @@ struct Operand {
   }
 };
 
-// w_b = M_b^-1 sum_{c in b} D_cb x_c   (force and torque of body b)
+// w_b = M_b^-1 sum_{c in b} D_cb x_c   (force and torque of body b).
+// Incidences are taken in batches (4 in FP32, 2 in FP64): their codes first,
+// then all record and operand loads of the batch, so they are in flight together.
 template <class T, class X>
 __device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int b) {
   T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
   const int e = __ldg(s.bptr + b + 1);
-#pragma unroll 2
-  for (int k = __ldg(s.bptr + b); k < e; ++k) {
-    const int code = __ldg(s.inc + k);
-    const int c = code >> 1;
-    const long long row = (long long)s.slots * c;
-    T R[16];
-    load_rec(s.rec, c, R);
-    const T x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
-    T f0 = R[0] * x0 + R[3] * x1 + R[6] * x2;
-    T f1 = R[1] * x0 + R[4] * x1 + R[7] * x2;
-    T f2 = R[2] * x0 + R[5] * x1 + R[8] * x2;
-    const bool side_b = (code & 1) != 0;
-    const T a0 = side_b ? R[12] : R[9], a1 = side_b ? R[13] : R[10], a2 = side_b ? R[14] : R[11];
-    const T sg = side_b ? T(1) : T(-1);
-    f0 *= sg;
-    f1 *= sg;
-    f2 *= sg;
-    F0 += f0;
-    F1 += f1;
-    F2 += f2;
-    Q0 += a1 * f2 - a2 * f1;
-    Q1 += a2 * f0 - a0 * f2;
-    Q2 += a0 * f1 - a1 * f0;
+  constexpr int NB = sizeof(T) == 8 ? 2 : 4;  // batch size within the register budget
+  for (int k0 = __ldg(s.bptr + b); k0 < e; k0 += NB) {
+    int code[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) code[j] = (k0 + j < e) ? __ldg(s.inc + k0 + j) : -1;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (code[j] < 0) continue;
+      const int c = code[j] >> 1;
+      const long long row = (long long)s.slots * c;
+      T R[16];
+      load_rec(s.rec, c, R);
+      const T x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
+      T f0 = R[0] * x0 + R[3] * x1 + R[6] * x2;
+      T f1 = R[1] * x0 + R[4] * x1 + R[7] * x2;
+      T f2 = R[2] * x0 + R[5] * x1 + R[8] * x2;
+      const bool side_b = (code[j] & 1) != 0;
+      const T a0 = side_b ? R[12] : R[9], a1 = side_b ? R[13] : R[10], a2 = side_b ? R[14] : R[11];
+      const T sg = side_b ? T(1) : T(-1);
+      f0 *= sg;
+      f1 *= sg;
+      f2 *= sg;
+      F0 += f0;
+      F1 += f1;
+      F2 += f2;
+      Q0 += a1 * f2 - a2 * f1;
+      Q1 += a2 * f0 - a0 * f2;
+      Q2 += a0 * f1 - a1 * f0;
+    }
   }
   const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
   T v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
@@ -364,6 +372,7 @@ struct PcgArgs {
   void* q;
   const void* dinv;         // Jacobi diagonal inverse (type T)
   int use_qtt;
+  int qtt_scaled;           // preconditioner is D^-1/2 X D^-1/2 (X approximates the scaled inverse)
   QttDev qtt;
   void* qw0;                // QTT work buffers (type T), rmax * P each
   void* qw1;
@@ -382,19 +391,34 @@ __device__ __forceinline__ const SysView<double>& sys_of<double>(const PcgArgs& 
 template <>
 __device__ __forceinline__ const SysView<float>& sys_of<float>(const PcgArgs& a) { return a.s32; }
 
-// z = X r through the QTT cores (d grid-synchronised steps).
+// z = X r through the QTT cores (d grid-synchronised steps).  For a Jacobi-
+// scaled preconditioner z = D^-1/2 X D^-1/2 r, the scalings taken from the
+// Jacobi diagonal inverse (sqrt(dinv) = D^-1/2).
 template <class T, class TC>
 __device__ bool qtt_precond(const PcgArgs& A, const T* r, T* z) {
   const QttDev& q = A.qtt;
   const long long items = A.P >> 1;
   const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const T* dinv = static_cast<const T*>(A.dinv);
   const T* in = r;
+  if (A.qtt_scaled) {
+    // the last core's step reads this buffer and writes qw0; qw1 is free until the next step
+    T* tmp = static_cast<T*>(A.qw1);
+    for (long long i = tid; i < A.P; i += gsz) tmp[i] = i < A.nrow ? sqrt(dinv[i]) * r[i] : T(0);
+    if (!grid_barrier(A.ctl, gridDim.x)) return false;
+    in = tmp;
+  }
+  __shared__ T gc[4 * 16 * 16];
   for (int k = q.d; k >= 1; --k) {
     T* out = (k == 1) ? z : static_cast<T*>(((q.d - k) & 1) ? A.qw1 : A.qw0);
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items; it += gsz)
-      qtt_step_any<T, T, TC>(q, k, in, out, it);
+    qtt_step_grid<T, T, TC>(q, k, in, out, items, gc, 4 * 16 * 16);
     if (!grid_barrier(A.ctl, gridDim.x)) return false;
     in = out;
+  }
+  if (A.qtt_scaled) {
+    for (long long i = tid; i < A.nrow; i += gsz) z[i] *= sqrt(dinv[i]);
+    if (!grid_barrier(A.ctl, gridDim.x)) return false;
   }
   return true;
 }
@@ -466,16 +490,33 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
     if (!(pq > 0.0)) return 2;
     const double alpha = rz / pq;
     double a3[2] = {0.0, 0.0};
-    for (long long i = tid; i < nrow; i += gsz) {
-      T pi = pnew[i];
-      e[i] += (T)alpha * pi;
-      T ri = r[i] - (T)alpha * q[i];
-      r[i] = ri;
-      a3[0] += (double)ri * (double)ri;
-      if (!A.use_qtt) {
-        T zi = dinv[i] * ri;
-        z[i] = zi;
-        a3[1] += (double)ri * (double)zi;
+    // several rows per thread and pass: every load of the batch before any store
+    constexpr int RB = sizeof(T) == 8 ? 2 : 4;
+    for (long long i0 = tid; i0 < nrow; i0 += RB * gsz) {
+      T pv[RB], ev[RB], rv[RB], qv[RB], dv[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const long long i = i0 + j * gsz;
+        const bool in = i < nrow;
+        pv[j] = in ? pnew[i] : T(0);
+        ev[j] = in ? e[i] : T(0);
+        rv[j] = in ? r[i] : T(0);
+        qv[j] = in ? q[i] : T(0);
+        dv[j] = in ? dinv[i] : T(0);
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const long long i = i0 + j * gsz;
+        if (i >= nrow) break;
+        e[i] = ev[j] + (T)alpha * pv[j];
+        const T ri = rv[j] - (T)alpha * qv[j];
+        r[i] = ri;
+        a3[0] += (double)ri * (double)ri;
+        if (!A.use_qtt) {
+          const T zi = dv[j] * ri;
+          z[i] = zi;
+          a3[1] += (double)ri * (double)zi;
+        }
       }
     }
     block_partials<2>(a3, A.partial, 3);
@@ -1201,6 +1242,11 @@ __global__ void k_diag(SysView<double> s, const double* __restrict__ H, double* 
   }
 }
 
+__global__ void k_sqrt_into(const double* __restrict__ dinv, double* __restrict__ out, long long P) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x)
+    out[i] = sqrt(dinv[i]);
+}
+
 // ------------------------------------------------------------------ PDIP kernels
 struct PdipArgs {
   SysView<double> s;
@@ -1434,6 +1480,15 @@ void launch_schur_blocks(qp_ctx* c, const double* gamma, const double* lambda) {
   QP_CUDA(cudaGetLastError());
 }
 
+// rowscale[i] = diag(S)_i^-1/2 for the current Schur blocks (dummy rows: 1).
+void launch_rowscale(qp_ctx* c, double* rowscale) {
+  SysView<double> s64 = view64(c, true);
+  k_diag<<<c->num_sms * 4, 256, 0, c->stream>>>(s64, c->H.as<double>(), c->dinv.as<double>(), c->dinv32.as<float>(),
+                                                c->P);
+  k_sqrt_into<<<c->num_sms * 4, 256, 0, c->stream>>>(c->dinv.as<double>(), rowscale, c->P);
+  QP_CUDA(cudaGetLastError());
+}
+
 void launch_apply64(qp_ctx* c, const double* x, double* y, bool with_H) {
   SysView<double> s = view64(c, with_H);
   int g = c->num_sms * 8;
@@ -1612,6 +1667,7 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   A.q = (mixed ? c->v32[5] : c->v64[7]).ensure(2 * P * es);  // q and the second search direction
   A.dinv = mixed ? (const void*)c->dinv32.p : (const void*)c->dinv.p;
   A.use_qtt = use_qtt ? 1 : 0;
+  A.qtt_scaled = (use_qtt && o->X->scaled) ? 1 : 0;
   A.qw0 = A.qw1 = nullptr;
   A.krylov = o->krylov == QP_BICGSTAB ? QP_BICGSTAB : QP_CG;
   A.xb = A.krylov == QP_BICGSTAB ? c->dm[12].ensure(5 * P * es) : nullptr;
@@ -1809,9 +1865,12 @@ int pdip_step(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, qp_pdip_stats* st
     // compress S_k and invert it, warm-started from the previous inverse
     // (Sec. 3.3: S_{k+1} = S_k + L_k with L_k block diagonal)
     QP_CUDA(cudaEventRecord(c->ev0, c->stream));
-    qtt_t S = nullptr;
-    int rc = qtt_compress(c, st, o->qtt_eps, o->qtt_rmax, &S);
-    if (rc != QP_OK) throw Error{rc, "pdip_step: qtt_compress failed: " + c->last_error};
+    // compress the Jacobi-scaled Schur matrix D^-1/2 S D^-1/2 (unit diagonal, dummy
+    // rows included), so that relative TT accuracy is not dominated by a few rows
+    double* rs = static_cast<double*>(c->dm[13].ensure((size_t)c->P * sizeof(double)));
+    launch_rowscale(c, rs);
+    qtt_t S = compress_impl(c, true, o->qtt_eps, o->qtt_rmax, rs);
+    int rc = QP_OK;
     qtt_t warm = so.X ? so.X : c->last_inv;
     if (warm && warm->d != S->d) warm = nullptr;
     qtt_t X = nullptr;

@@ -8,11 +8,12 @@
 namespace qp {
 namespace {
 
+constexpr int QTT_GCAP = 4 * 16 * 16;  // staged core values (ranks up to 16)
+
 template <class TV, class TA, class TC>
 __global__ void k_qtt_step(QttDev q, int k, const TV* in, TV* out, long long items) {
-  const long long gsz = (long long)gridDim.x * blockDim.x;
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items; it += gsz)
-    qtt_step_any<TV, TA, TC>(q, k, in, out, it);
+  __shared__ TA gc[QTT_GCAP];
+  qtt_step_grid<TV, TA, TC>(q, k, in, out, items, gc, QTT_GCAP);
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
@@ -103,7 +104,10 @@ void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype cdt
   void* w0 = c->scratch[5].ensure((size_t)N * q.rmax * es);
   void* w1 = c->scratch[6].ensure((size_t)N * q.rmax * es);
   const long long items = N >> 1;
-  const int grid = (int)((items + 255) / 256 < (long long)c->num_sms * 16 ? (items + 255) / 256 : (long long)c->num_sms * 16);
+  // two columns per thread
+  long long want = (items + 511) / 512;
+  if (want > (long long)c->num_sms * 16) want = (long long)c->num_sms * 16;
+  const int grid = (int)(want < 1 ? 1 : want);
   const void* in = x;
   for (int k = A->d; k >= 1; --k) {
     void* out = (k == 1) ? y : (((A->d - k) & 1) ? w1 : w0);

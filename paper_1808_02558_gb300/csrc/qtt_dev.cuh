@@ -130,4 +130,82 @@ __device__ __forceinline__ void qtt_step_any(const QttDev& q, int k, const TV* i
   else qtt_step_item<TV, TA, TC>(q, k, in, out, item);
 }
 
+// Block-level step: the core (converted to TA) is staged in shared memory once
+// per block, and each thread computes two columns (items it and it + stride),
+// so every core value read from shared memory feeds two columns.  All threads of
+// the block must call it (it synchronises).  gc: shared buffer of at least
+// r_{k-1} * 4 * r_k values.  Requires r_k <= R.
+template <int R, class TV, class TA, class TC>
+__device__ __forceinline__ void qtt_step_block(const QttDev& q, int k, const TV* in, TV* out, long long items,
+                                               TA* gc, long long first, long long stride) {
+  const int d = q.d;
+  const int r0 = q.ranks[k - 1], r1 = q.ranks[k];
+  const TC* G = static_cast<const TC*>(q.cores) + q.off[k - 1];
+  const int ncore = r0 * 4 * r1;
+  for (int i = threadIdx.x; i < ncore; i += blockDim.x) {
+    if constexpr (sizeof(TC) == 8) gc[i] = (TA)G[i];
+    else gc[i] = (TA)core_f<TC>(G, i);
+  }
+  __syncthreads();
+  const int lowbits = d - k;
+  const long long nI = 1LL << lowbits;
+  for (long long it = first; it < items; it += 2 * stride) {
+    const long long it2 = it + stride;
+    const bool two = it2 < items;
+    TA v0[R], v1[R], u0[R], u1[R];
+    const long long I = it & (nI - 1), Jp = it >> lowbits;
+    const long long I2 = it2 & (nI - 1), Jp2 = it2 >> lowbits;
+    const TV* a0 = in + ((2 * Jp) * r1) * nI + I;
+    const TV* a1 = in + ((2 * Jp + 1) * r1) * nI + I;
+    const TV* b0 = in + ((2 * Jp2) * r1) * nI + I2;
+    const TV* b1 = in + ((2 * Jp2 + 1) * r1) * nI + I2;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const bool ok = b < r1;
+      v0[b] = ok ? (TA)a0[(long long)b * nI] : TA(0);
+      v1[b] = ok ? (TA)a1[(long long)b * nI] : TA(0);
+      u0[b] = (ok && two) ? (TA)b0[(long long)b * nI] : TA(0);
+      u1[b] = (ok && two) ? (TA)b1[(long long)b * nI] : TA(0);
+    }
+    TV* o = out + (Jp * r0) * (2 * nI) + I;
+    TV* o2 = out + (Jp2 * r0) * (2 * nI) + I2;
+    for (int a = 0; a < r0; ++a) {
+      const TA* Ga = gc + a * 4 * r1;
+      TA p0 = 0, p1 = 0, q0 = 0, q1 = 0;
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        if (b < r1) {
+          const TA g00 = Ga[b], g01 = Ga[r1 + b], g10 = Ga[2 * r1 + b], g11 = Ga[3 * r1 + b];
+          p0 += g00 * v0[b] + g01 * v1[b];
+          p1 += g10 * v0[b] + g11 * v1[b];
+          q0 += g00 * u0[b] + g01 * u1[b];
+          q1 += g10 * u0[b] + g11 * u1[b];
+        }
+      }
+      o[(long long)a * 2 * nI] = (TV)p0;
+      o[(long long)a * 2 * nI + nI] = (TV)p1;
+      if (two) {
+        o2[(long long)a * 2 * nI] = (TV)q0;
+        o2[(long long)a * 2 * nI + nI] = (TV)q1;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Block-level dispatch on the input rank; falls back to the per-item step
+// (cores read from global memory) for ranks above 32 or cores larger than gcap.
+template <class TV, class TA, class TC>
+__device__ __forceinline__ void qtt_step_grid(const QttDev& q, int k, const TV* in, TV* out, long long items,
+                                              TA* gc, int gcap) {
+  const int r0 = q.ranks[k - 1], r1 = q.ranks[k];
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (r0 * 4 * r1 <= gcap) {
+    if (r1 <= 8) return qtt_step_block<8, TV, TA, TC>(q, k, in, out, items, gc, first, stride);
+    if (r1 <= 16) return qtt_step_block<16, TV, TA, TC>(q, k, in, out, items, gc, first, stride);
+  }
+  for (long long it = first; it < items; it += stride) qtt_step_any<TV, TA, TC>(q, k, in, out, it);
+}
+
 }  // namespace qp

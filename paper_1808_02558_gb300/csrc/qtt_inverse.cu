@@ -738,6 +738,7 @@ qp_qtt* inverse_impl(qp_ctx* c, qp_qtt* S, double eps, int rmax, int sweeps, qp_
   }
   cudaFree(Xr->cores);
   delete Xr;
+  out->scaled = S->scaled;
   return out;
 }
 

@@ -325,9 +325,14 @@ struct EntryArgs {
   const int* inc;
   const double* H;    // [6][Nc] or null
   const int* off;     // [M+1] offsets of off-diagonal blocks (per body)
+  const double* rs;   // [P] row scaling (entry (i,j) is multiplied by rs[i] rs[j]) or null
   unsigned long long* key;
   double* val;
 };
+
+__device__ __forceinline__ double escale(const EntryArgs& e, long long i, long long j) {
+  return e.rs ? e.rs[i] * e.rs[j] : 1.0;
+}
 
 __global__ void k_entries_offdiag(EntryArgs e) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -345,8 +350,9 @@ __global__ void k_entries_offdiag(EntryArgs e) {
       body_block(R1, s1, e.rec + (size_t)c2 * 16, s2, im, iI, blk);
       for (int u = 0; u < 3; ++u)
         for (int v = 0; v < 3; ++v) {
-          e.key[o] = qtt_key((unsigned long long)e.slots * c1 + u, (unsigned long long)e.slots * c2 + v, e.d);
-          e.val[o] = blk[3 * u + v];
+          const long long ri = (long long)e.slots * c1 + u, ci = (long long)e.slots * c2 + v;
+          e.key[o] = qtt_key((unsigned long long)ri, (unsigned long long)ci, e.d);
+          e.val[o] = blk[3 * u + v] * escale(e, ri, ci);
           ++o;
         }
     }
@@ -374,13 +380,14 @@ __global__ void k_entries_diag(EntryArgs e, long long base) {
   long long o = base + (long long)per * c;
   for (int u = 0; u < 3; ++u)
     for (int v = 0; v < 3; ++v) {
-      e.key[o] = qtt_key((unsigned long long)e.slots * c + u, (unsigned long long)e.slots * c + v, e.d);
-      e.val[o] = blk[3 * u + v];
+      const long long ri = (long long)e.slots * c + u, ci = (long long)e.slots * c + v;
+      e.key[o] = qtt_key((unsigned long long)ri, (unsigned long long)ci, e.d);
+      e.val[o] = blk[3 * u + v] * escale(e, ri, ci);
       ++o;
     }
   if (e.slots == 4) {
     e.key[o] = qtt_key(4ull * c + 3, 4ull * c + 3, e.d);
-    e.val[o] = 1.0;
+    e.val[o] = escale(e, 4LL * c + 3, 4LL * c + 3);
   }
 }
 
@@ -389,7 +396,7 @@ __global__ void k_entries_tail(EntryArgs e, long long base) {
   for (long long i = t0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < e.P;
        i += (long long)gridDim.x * blockDim.x) {
     e.key[base + i - t0] = qtt_key((unsigned long long)i, (unsigned long long)i, e.d);
-    e.val[base + i - t0] = 1.0;
+    e.val[base + i - t0] = escale(e, i, i);
   }
 }
 
@@ -543,6 +550,7 @@ qp_qtt* tt_round_impl(qp_ctx* c, const qp_qtt* A, double eps, int rmax) {
   QP_CUDA(cudaMemcpyAsync(r.data(), ranks, (d + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   QP_CUDA(cudaStreamSynchronize(c->stream));
   qp_qtt* out = qtt_alloc(c, d, r);
+  out->scaled = A->scaled;
   for (int k = 0; k < d; ++k)
     QP_CUDA(cudaMemcpyAsync(out->cores + out->offset[k], cores + (size_t)k * cap,
                             (out->offset[k + 1] - out->offset[k]) * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -552,7 +560,7 @@ qp_qtt* tt_round_impl(qp_ctx* c, const qp_qtt* A, double eps, int rmax) {
 }
 
 // Right-to-left sparse TT-SVD of the padded Schur matrix (or N when H == null).
-qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax) {
+qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax, const double* rowscale) {
   QP_REQUIRE(c->have_contacts, QP_NOT_READY, "qtt_compress: no contacts");
   QP_REQUIRE(eps >= 0 && rmax >= 1, QP_INVALID_ARG, "qtt_compress: eps >= 0 and rmax >= 1 required");
   if (rmax > 128) rmax = 128;  // unfoldings have 4 r columns; the one-block eigensolver takes n <= 512
@@ -594,6 +602,7 @@ qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax) {
   e.inc = c->inc.as<int>();
   e.H = with_H ? c->H.as<double>() : nullptr;
   e.off = off;
+  e.rs = rowscale;
   e.key = key;
   e.val = val;
   if (M > 0) k_entries_offdiag<<<ceil_div(M, 128), 128, 0, st>>>(e);
@@ -695,6 +704,7 @@ qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax) {
                             (out->offset[k + 1] - out->offset[k]) * sizeof(double), cudaMemcpyDeviceToDevice, st));
   QP_CUDA(cudaStreamSynchronize(st));
   for (auto& b : cb_store) b.release();
+  out->scaled = rowscale ? 1 : 0;
   return out;
 }
 
@@ -724,7 +734,7 @@ int qtt_compress(qp_ctx_t c, const qp_state* st, double eps, int rmax, qtt_t* ou
       QP_REQUIRE(st->gamma && st->lambda, QP_INVALID_ARG, "qtt_compress: state with null gamma/lambda");
       launch_schur_blocks(c, st->gamma, st->lambda);
     }
-    *out = compress_impl(c, st != nullptr, eps, rmax);
+    *out = compress_impl(c, st != nullptr, eps, rmax, nullptr);
   } catch (const Error& e) {
     set_error(c, e);
     return e.code;
