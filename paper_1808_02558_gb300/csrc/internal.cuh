@@ -42,16 +42,13 @@ struct Buf {
 
 // Device-side control block of the persistent kernels.
 struct DevCtl {
-  unsigned int bar_count;  // grid barrier arrivals
-  unsigned int bar_gen;    // grid barrier generation
+  unsigned int bar_count;  // grid barrier: arrivals so far (monotonic within a launch)
+  unsigned int pad0_[31];  // keeps the polled counter on its own cache line
   int err;                 // 0 or a QP_* code set by a device-side failure
   int iters;               // Krylov iterations
   int outer;               // refinement steps
   int halvings;
   double scal[16];         // scalars handed between kernels (eta, t, s, norms, ...)
-  unsigned int release;    // flag barrier: generation released by block 0
-  unsigned int pad_[31];
-  unsigned int flags[4096];// flag barrier: generation reached by each block
 };
 
 enum Scal { S_ETA = 0, S_T, S_RDUAL, S_RT, S_S, S_RELRES, S_BNORM, S_SMAX, S_RCENT };

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <vector>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "qtt_dev.cuh"
 
@@ -34,70 +36,62 @@ constexpr long long BARRIER_BUDGET = 4000000000LL;  // clock64 ticks (~2 s) per 
 
 // ------------------------------------------------------------------ barrier
 // Grid barrier with a bounded wait: on expiry it records QP_TIMEOUT in ctl->err
-// and returns false; callers leave the kernel.  Also returns false once any
-// block has recorded an error.
+// and returns false; callers leave the kernel.  A block that finds the error
+// flag set while it waits also returns false.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Flag barrier: block i publishes generation g in flags[i]; block 0 waits for
-// every flag (one polling thread per block), then publishes g in `release`,
-// which the other blocks poll.  No two blocks write the same word, so arrivals
-// do not serialise on an atomic.  Every wait is bounded by BARRIER_BUDGET; on
-// expiry QP_TIMEOUT is recorded and false is returned.
-__device__ bool grid_barrier(DevCtl* ctl, unsigned nblocks) {
+// Counter barrier: after a __syncthreads (which orders the writes of the whole
+// block before thread 0's release), thread 0 of every block adds 1 to
+// ctl->bar_count and polls it with acquire loads until it reaches
+// generation x nblocks; a second __syncthreads hands the acquired state to the
+// rest of the block.  The counter starts at 0 (the control block is cleared
+// before every launch) and each block counts its generations in shared memory
+// (every cooperative kernel calls barrier_init first).  One poller per block
+// on one word keeps the polling traffic low.
+__shared__ unsigned g_bar_gen;
+
+__device__ __forceinline__ void barrier_init() {
+  if (threadIdx.x == 0) g_bar_gen = 0;
+  __syncthreads();
+}
+
+// Thread 0 only: arrive and wait (bounded).  Returns false on timeout or when
+// another block has recorded an error.
+__device__ __forceinline__ bool barrier_arrive_wait(DevCtl* ctl, unsigned nblocks, long long budget) {
+  const unsigned gen = g_bar_gen + 1u;
+  g_bar_gen = gen;
+  red_release_add(&ctl->bar_count, 1u);
+  const unsigned target = gen * nblocks;
+  if ((int)(ld_acquire(&ctl->bar_count) - target) >= 0) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if ((int)(ld_acquire(&ctl->bar_count) - target) >= 0) return true;
+    if (*(volatile int*)&ctl->err) return false;
+    if (clock64() - t0 > budget) {
+      atomicCAS(&ctl->err, 0, QP_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ bool grid_barrier(DevCtl* ctl, unsigned nblocks, long long budget = BARRIER_BUDGET) {
   __shared__ int ok;
-  __shared__ unsigned gen_s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    gen_s = ld_acquire(&ctl->flags[blockIdx.x]) + 1u;
-    __threadfence();
-    st_release(&ctl->flags[blockIdx.x], gen_s);
-    ok = 1;
-  }
-  __syncthreads();
-  const unsigned gen = gen_s;
-  if (blockIdx.x == 0) {
-    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
-      long long t0 = clock64();
-      while ((int)(ld_acquire(&ctl->flags[b]) - gen) < 0) {
-        if (clock64() - t0 > BARRIER_BUDGET) {
-          atomicCAS(&ctl->err, 0, QP_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release(&ctl->release, gen);
-    }
-  } else if (threadIdx.x == 0) {
-    long long t0 = clock64();
-    while ((int)(ld_acquire(&ctl->release) - gen) < 0) {
-      if (clock64() - t0 > BARRIER_BUDGET) {
-        atomicCAS(&ctl->err, 0, QP_TIMEOUT);
-        ok = 0;
-        break;
-      }
-    }
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (*(volatile int*)&ctl->err) ok = 0;
-  }
+  if (threadIdx.x == 0) ok = barrier_arrive_wait(ctl, nblocks, budget) ? 1 : 0;
   __syncthreads();
   return ok != 0;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
@@ -106,12 +100,15 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
-// Block-reduce n values (sum) and store them as this block's partials.
-template <int N>
-__device__ void block_partials(double (&v)[N], double* partial, int slot0, bool is_min = false) {
+// Block-reduce n values (sum) and store them as this block's partials.  The
+// per-thread and per-warp sums are taken in the accumulator type V (float in
+// the FP32 inner solves, where FP64 arithmetic is a slow pipe, double
+// elsewhere); warps are combined in double.
+template <int N, class V>
+__device__ void block_partials(V (&v)[N], double* partial, int slot0, bool is_min = false) {
   __shared__ double sm[N][NWMAX];
   for (int k = 0; k < N; ++k) {
-    double x = is_min ? warp_min(v[k]) : warp_sum(v[k]);
+    double x = is_min ? warp_min((double)v[k]) : (double)warp_sum(v[k]);
     if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = x;
   }
   __syncthreads();
@@ -144,6 +141,41 @@ __device__ double grid_total(const double* partial, int slot, bool is_min = fals
   double out = res;
   __syncthreads();
   return out;
+}
+
+// Grid barrier that also forms the totals of K consecutive partial slots
+// (written by block_partials before the barrier) in the same pass over the
+// blocks.  Every block adds the same values in the same order, so all blocks
+// obtain bit-identical totals.
+template <int K>
+__device__ bool grid_barrier_total(DevCtl* ctl, unsigned nblocks, const double* partial, int slot,
+                                   double (&out)[K], long long budget = BARRIER_BUDGET) {
+  __shared__ double sm[K][NWMAX];
+  __shared__ double res[K];
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) ok = barrier_arrive_wait(ctl, nblocks, budget) ? 1 : 0;
+  __syncthreads();
+  const bool good = ok != 0;
+  double x[K];
+  for (int k = 0; k < K; ++k) x[k] = 0.0;
+  if (good)
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
+      for (int k = 0; k < K; ++k) x[k] += *(volatile const double*)&partial[(size_t)b * NRED + slot + k];
+  for (int k = 0; k < K; ++k) {
+    const double v = warp_sum(x[k]);
+    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[threadIdx.x][w];
+    res[threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int k = 0; k < K; ++k) out[k] = res[k];
+  __syncthreads();
+  return good;
 }
 
 // ------------------------------------------------------------------ operator
@@ -249,7 +281,7 @@ __device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int
 // If xout is set, the operand value of row i is also stored there (the
 // materialised search direction).
 template <class T, class X>
-__device__ __forceinline__ double contact_apply(const SysView<T>& s, const X& x, T* y, int c, T* xout = nullptr) {
+__device__ __forceinline__ T contact_apply(const SysView<T>& s, const X& x, T* y, int c, T* xout = nullptr) {
   const long long n = s.Nc;
   const int a = __ldg(s.ca + c), b = __ldg(s.cb + c);
   T R[16];
@@ -282,7 +314,7 @@ __device__ __forceinline__ double contact_apply(const SysView<T>& s, const X& x,
   y[row] = y0;
   y[row + 1] = y1;
   y[row + 2] = y2;
-  double dot = (double)x0 * (double)y0 + (double)x1 * (double)y1 + (double)x2 * (double)y2;
+  T dot = x0 * y0 + x1 * y1 + x2 * y2;
   if (xout) {
     xout[row] = x0;
     xout[row + 1] = x1;
@@ -292,7 +324,7 @@ __device__ __forceinline__ double contact_apply(const SysView<T>& s, const X& x,
     const T x3 = x(row + 3);
     y[row + 3] = x3;
     if (xout) xout[row + 3] = x3;
-    dot += (double)x3 * (double)x3;
+    dot += x3 * x3;
   }
   return dot;
 }
@@ -430,6 +462,16 @@ __device__ bool qtt_precond(const PcgArgs& A, const T* r, T* z) {
 // is never materialised before the operator: the body gather forms it on the
 // fly from (z, p_{k-1}), and the contact pass stores it into the other p buffer
 // while it computes q = S p_k.
+// TC = void instantiates the Jacobi-only solver: no QTT code, fewer registers.
+template <class TC>
+constexpr bool kQtt = !std::is_void_v<TC>;
+
+template <class T, class TC>
+__device__ __forceinline__ bool qtt_precond_if(const PcgArgs& A, const T* in, T* out) {
+  if constexpr (kQtt<TC>) return qtt_precond<T, TC>(A, in, out);
+  else return false;
+}
+
 template <class T, class TC>
 __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   const SysView<T>& s = sys_of<T>(A);
@@ -447,27 +489,28 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
   const unsigned nb = gridDim.x;
 
   // setup: e = 0, r = b, z = M^-1 r
-  double acc[2] = {0.0, 0.0};
+  T acc[2] = {};
   for (long long i = tid; i < nrow; i += gsz) {
     T bi = b[i];
     e[i] = 0;
     r[i] = bi;
-    acc[0] += (double)bi * (double)bi;
-    if (!A.use_qtt) {
+    acc[0] += bi * bi;
+    if (!(kQtt<TC> && A.use_qtt)) {
       T zi = dinv[i] * bi;
       z[i] = zi;
-      acc[1] += (double)bi * (double)zi;
+      acc[1] += bi * zi;
     }
   }
   block_partials<2>(acc, A.partial, 0);
-  if (!grid_barrier(A.ctl, nb)) return -1;
-  const double bb = grid_total(A.partial, 0);
-  double rz = grid_total(A.partial, 1);
+  double t0[2];
+  if (!grid_barrier_total<2>(A.ctl, nb, A.partial, 0, t0)) return -1;
+  const double bb = t0[0];
+  double rz = t0[1];
   if (bb == 0.0) return 0;
-  if (A.use_qtt) {
-    if (!qtt_precond<T, TC>(A, r, z)) return -1;
-    double a1[1] = {0.0};
-    for (long long i = tid; i < nrow; i += gsz) a1[0] += (double)r[i] * (double)z[i];
+  if ((kQtt<TC> && A.use_qtt)) {
+    if (!qtt_precond_if<T, TC>(A, r, z)) return -1;
+    T a1[1] = {};
+    for (long long i = tid; i < nrow; i += gsz) a1[0] += r[i] * z[i];
     block_partials<1>(a1, A.partial, 1);
     if (!grid_barrier(A.ctl, nb)) return -1;
     rz = grid_total(A.partial, 1);
@@ -482,14 +525,53 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
     // q = S p_k
     for (int bd = (int)tid; bd < s.M; bd += (int)gsz) body_gather(s, dir, bd);
     if (!grid_barrier(A.ctl, nb)) return -1;
-    double a2[1] = {0.0};
+    T a2[1] = {};
     for (int c = (int)tid; c < s.Nc; c += (int)gsz) a2[0] += contact_apply(s, dir, q, c, pnew);
     block_partials<1>(a2, A.partial, 2);
-    if (!grid_barrier(A.ctl, nb)) return -1;
-    const double pq = grid_total(A.partial, 2);
+    double t2[1];
+    if (!grid_barrier_total<1>(A.ctl, nb, A.partial, 2, t2)) return -1;
+    const double pq = t2[0];
     if (!(pq > 0.0)) return 2;
     const double alpha = rz / pq;
-    double a3[2] = {0.0, 0.0};
+    T a3[2] = {};
+    bool updated = false;
+    if constexpr (sizeof(T) == 4) {
+      if (!(kQtt<TC> && A.use_qtt)) {
+        // FP32 Jacobi: four rows per thread with float4 loads and stores (all
+        // buffers are allocated with P >= round_up(nrow, 4) values, 16-byte aligned)
+        const long long n4 = nrow >> 2;
+        const float4* P4 = reinterpret_cast<const float4*>(pnew);
+        const float4* Q4 = reinterpret_cast<const float4*>(q);
+        const float4* D4 = reinterpret_cast<const float4*>(dinv);
+        float4* E4 = reinterpret_cast<float4*>(e);
+        float4* R4 = reinterpret_cast<float4*>(r);
+        float4* Z4 = reinterpret_cast<float4*>(z);
+        const float al = (float)alpha;
+        for (long long i = tid; i < n4; i += gsz) {
+          const float4 pv = P4[i], qv = Q4[i], dv = D4[i];
+          float4 ev = E4[i], rv = R4[i];
+          ev.x += al * pv.x; ev.y += al * pv.y; ev.z += al * pv.z; ev.w += al * pv.w;
+          rv.x -= al * qv.x; rv.y -= al * qv.y; rv.z -= al * qv.z; rv.w -= al * qv.w;
+          const float4 zv = make_float4(dv.x * rv.x, dv.y * rv.y, dv.z * rv.z, dv.w * rv.w);
+          E4[i] = ev;
+          R4[i] = rv;
+          Z4[i] = zv;
+          a3[0] += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+          a3[1] += rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
+        }
+        for (long long i = (n4 << 2) + tid; i < nrow; i += gsz) {
+          e[i] += (T)alpha * pnew[i];
+          const T ri = r[i] - (T)alpha * q[i];
+          r[i] = ri;
+          const T zi = dinv[i] * ri;
+          z[i] = zi;
+          a3[0] += ri * ri;
+          a3[1] += ri * zi;
+        }
+        updated = true;
+      }
+    }
+    if (!updated) {
     // several rows per thread and pass: every load of the batch before any store
     constexpr int RB = sizeof(T) == 8 ? 2 : 4;
     for (long long i0 = tid; i0 < nrow; i0 += RB * gsz) {
@@ -511,29 +593,31 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
         e[i] = ev[j] + (T)alpha * pv[j];
         const T ri = rv[j] - (T)alpha * qv[j];
         r[i] = ri;
-        a3[0] += (double)ri * (double)ri;
-        if (!A.use_qtt) {
+        a3[0] += ri * ri;
+        if (!(kQtt<TC> && A.use_qtt)) {
           const T zi = dv[j] * ri;
           z[i] = zi;
-          a3[1] += (double)ri * (double)zi;
+          a3[1] += ri * zi;
         }
       }
     }
+    }
     block_partials<2>(a3, A.partial, 3);
-    if (!grid_barrier(A.ctl, nb)) return -1;
+    double t3[2];
+    if (!grid_barrier_total<2>(A.ctl, nb, A.partial, 3, t3)) return -1;
     ++iters;
-    const double rr = grid_total(A.partial, 3);
+    const double rr = t3[0];
     double rz_new;
     if (rr <= stop) return 0;
-    if (A.use_qtt) {
-      if (!qtt_precond<T, TC>(A, r, z)) return -1;
-      double a4[1] = {0.0};
-      for (long long i = tid; i < nrow; i += gsz) a4[0] += (double)r[i] * (double)z[i];
+    if ((kQtt<TC> && A.use_qtt)) {
+      if (!qtt_precond_if<T, TC>(A, r, z)) return -1;
+      T a4[1] = {};
+      for (long long i = tid; i < nrow; i += gsz) a4[0] += r[i] * z[i];
       block_partials<1>(a4, A.partial, 5);
       if (!grid_barrier(A.ctl, nb)) return -1;
       rz_new = grid_total(A.partial, 5);
     } else {
-      rz_new = grid_total(A.partial, 4);
+      rz_new = t3[1];
     }
     beta = rz_new / rz;
     rz = rz_new;
@@ -558,7 +642,7 @@ __device__ bool op_apply(const PcgArgs& A, const SysView<T>& s, const T* x, T* y
 // out = M^-1 in: Jacobi or the QTT approximate inverse.
 template <class T, class TC>
 __device__ bool prec_apply(const PcgArgs& A, const T* in, T* out) {
-  if (A.use_qtt) return qtt_precond<T, TC>(A, in, out);
+  if ((kQtt<TC> && A.use_qtt)) return qtt_precond_if<T, TC>(A, in, out);
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const T* dinv = static_cast<const T*>(A.dinv);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.nrow; i += gsz) out[i] = dinv[i] * in[i];
@@ -587,7 +671,7 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int nrow = A.nrow;
   const unsigned nb = gridDim.x;
-  double a0[1] = {0.0};
+  T a0[1] = {};
   for (long long i = tid; i < P; i += gsz) {
     if (i < nrow) {
       const T bi = b[i];
@@ -595,7 +679,7 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
       r[i] = bi;
       rh[i] = bi;
       v[i] = 0;
-      a0[0] += (double)bi * (double)bi;
+      a0[0] += bi * bi;
     }
     p[i] = 0;   // the QTT preconditioner reads whole padded vectors
     sv[i] = 0;
@@ -614,19 +698,19 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
     if (!grid_barrier(A.ctl, nb)) return -1;
     if (!prec_apply<T, TC>(A, p, y)) return -1;
     if (!op_apply<T>(A, s, y, v)) return -1;
-    double a1[1] = {0.0};
-    for (long long i = tid; i < nrow; i += gsz) a1[0] += (double)rh[i] * (double)v[i];
+    T a1[1] = {};
+    for (long long i = tid; i < nrow; i += gsz) a1[0] += rh[i] * v[i];
     block_partials<1>(a1, A.partial, 9);
     if (!grid_barrier(A.ctl, nb)) return -1;
     const double rv = grid_total(A.partial, 9);
     if (rv == 0.0) return 2;
     alpha = rho / rv;
-    double a2[1] = {0.0};
+    T a2[1] = {};
     for (long long i = tid; i < nrow; i += gsz) {
       x[i] += (T)alpha * y[i];
       const T si = r[i] - (T)alpha * v[i];
       sv[i] = si;
-      a2[0] += (double)si * (double)si;
+      a2[0] += si * si;
     }
     block_partials<1>(a2, A.partial, 10);
     if (!grid_barrier(A.ctl, nb)) return -1;
@@ -636,23 +720,23 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
     }
     if (!prec_apply<T, TC>(A, sv, z)) return -1;
     if (!op_apply<T>(A, s, z, t)) return -1;
-    double a3[2] = {0.0, 0.0};
+    T a3[2] = {};
     for (long long i = tid; i < nrow; i += gsz) {
-      a3[0] += (double)t[i] * (double)sv[i];
-      a3[1] += (double)t[i] * (double)t[i];
+      a3[0] += t[i] * sv[i];
+      a3[1] += t[i] * t[i];
     }
     block_partials<2>(a3, A.partial, 11);
     if (!grid_barrier(A.ctl, nb)) return -1;
     const double ts = grid_total(A.partial, 11), tt = grid_total(A.partial, 12);
     if (!(tt > 0.0)) return 2;
     omega = ts / tt;
-    double a4[2] = {0.0, 0.0};
+    T a4[2] = {};
     for (long long i = tid; i < nrow; i += gsz) {
       x[i] += (T)omega * z[i];
       const T ri = sv[i] - (T)omega * t[i];
       r[i] = ri;
-      a4[0] += (double)rh[i] * (double)ri;
-      a4[1] += (double)ri * (double)ri;
+      a4[0] += rh[i] * ri;
+      a4[1] += ri * ri;
     }
     block_partials<2>(a4, A.partial, 13);
     if (!grid_barrier(A.ctl, nb)) return -1;
@@ -666,6 +750,7 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
 // FP64 outer refinement: r64 = rhs - S x; inner solve on r64/||r64||; x += ...
 template <class T, class TC>
 __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
+  barrier_init();
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -1003,27 +1088,6 @@ __device__ __forceinline__ const SysView<double>& fsys<double>(const FusedArgs& 
 template <>
 __device__ __forceinline__ const SysView<float>& fsys<float>(const FusedArgs& a) { return a.s32; }
 
-// Sum of three consecutive partial slots over all blocks, in one pass.
-__device__ void grid_total3(const double* partial, int slot, double (&out)[3]) {
-  __shared__ double sm[3][NWMAX];
-  __shared__ double res[3];
-  double x[3] = {0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-    for (int k = 0; k < 3; ++k) x[k] += *(volatile const double*)&partial[(size_t)b * NRED + slot + k];
-  for (int k = 0; k < 3; ++k) {
-    double v = warp_sum(x[k]);
-    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[threadIdx.x][w];
-    res[threadIdx.x] = t;
-  }
-  __syncthreads();
-  for (int k = 0; k < 3; ++k) out[k] = res[k];
-  __syncthreads();
-}
 
 // Pipelined Jacobi-PCG (Ghysels and Vanroose, Parallel Computing 40 (2014),
 // Alg. 3) on S_T e = b, x0 = 0, b in the state records.  One grid barrier per
@@ -1041,7 +1105,7 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
   const long long r0 = (long long)s.slots * c0, r1 = (long long)s.slots * c1;
   // phase I: e = 0, r = b, u = M^-1 b, p = q = s = 0, z = 0; w0 = S u -> pipe n[1]
   // (stored in the n slot of the other parity, moved to w[0] below)
-  double acc[3] = {0.0, 0.0, 0.0};
+  T acc[3] = {};
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     const T bi = sr[i * 8 + 6];
     T pv[8];
@@ -1051,31 +1115,29 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
     store8(sr + i * 8, ns);
     pr[i * 8 + 4] = T(0);
     pr[i * 8 + 5] = T(0);
-    acc[0] += (double)bi * (double)ui;
-    acc[1] += (double)bi * (double)bi;
+    acc[0] += bi * ui;
+    acc[1] += bi * bi;
   }
   // w0 = S M^-1 b into the n[1] slot of each row (no one reads n[1] in this phase)
   fused_apply(s, A.pt, OpRhs<T>{pr, sr}, pr + 3, 8, wl);
   block_partials<3>(acc, A.partial, 0);
-  if (!grid_barrier(A.ctl, nb)) return -1;
   double tot[3];
-  grid_total3(A.partial, 0, tot);
+  if (!grid_barrier_total<3>(A.ctl, nb, A.partial, 0, tot)) return -1;
   double gamma = tot[0];
   const double bb = tot[1];
   if (bb == 0.0) return 0;
   // phase 0: w[0] <- n[1] (own rows); n0 = S M^-1 w0 into n[0]; delta0 = (w0, u0)
-  double acc1[3] = {0.0, 0.0, 0.0};
+  T acc1[3] = {};
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     const T w0 = pr[i * 8 + 3];
     pr[i * 8 + 0] = w0;
-    acc1[0] += (double)w0 * (double)sr[i * 8 + 2];
+    acc1[0] += w0 * sr[i * 8 + 2];
   }
   __syncthreads();
   // other blocks read w0 of our rows through n[1]: use that slot as the operand
   fused_apply(s, A.pt, OpW<T>{pr, 3}, pr + 2, 8, wl);
   block_partials<3>(acc1, A.partial, 3);
-  if (!grid_barrier(A.ctl, nb)) return -1;
-  grid_total3(A.partial, 3, tot);
+  if (!grid_barrier_total<3>(A.ctl, nb, A.partial, 3, tot)) return -1;
   double delta = tot[0];
   if (!(gamma > 0.0) || !(delta > 0.0)) return 2;
   double alpha = gamma / delta, beta = 0.0;
@@ -1084,7 +1146,7 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
   for (int it = 0; it < maxit; ++it) {
     const T a = (T)alpha, bt = (T)beta;
     const int nxt = cur ^ 1;
-    double d3[3] = {0.0, 0.0, 0.0};
+    T d3[3] = {};
 #pragma unroll 2
     for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       T pv[8], st[8];
@@ -1106,9 +1168,9 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
       pr[i * 8 + 4 + cur] = zi;    // z[cur]
       const T ns[8] = {ei, ri, ui, pi, qi, si, st[6], T(0)};
       store8(sr + i * 8, ns);
-      d3[0] += (double)ri * (double)ui;
-      d3[1] += (double)wn * (double)ui;
-      d3[2] += (double)ri * (double)ri;
+      d3[0] += ri * ui;
+      d3[1] += wn * ui;
+      d3[2] += ri * ri;
     }
     // n_{i+1} = S M^-1 w_{i+1}, w_{i+1} formed on the fly from (w_i, n_i, z_{i-1})
     fused_apply(s, A.pt, OpPipe<T>{pr, cur, a, bt}, pr + 2 + nxt, 8, wl);
@@ -1116,9 +1178,8 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
     // already in the next iteration never overwrites sums still being read
     const int sl = 6 + 3 * (it & 1);
     block_partials<3>(d3, A.partial, sl);
-    if (!grid_barrier(A.ctl, nb)) return -1;
+    if (!grid_barrier_total<3>(A.ctl, nb, A.partial, sl, tot)) return -1;
     ++iters;
-    grid_total3(A.partial, sl, tot);
     const double gnew = tot[0], dnew = tot[1], rr = tot[2];
     if (rr <= stop) return 0;
     if (!(gnew > 0.0)) return 2;
@@ -1134,6 +1195,7 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
 
 template <class T>
 __global__ void __launch_bounds__(NT_FUSED, 1) k_pcg_fused(FusedArgs A) {
+  barrier_init();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1271,6 +1333,7 @@ struct PdipArgs {
 // gap, t, residual norms, Schur blocks and Newton rhs at (gamma, lambda).
 // mode 0: full pre-step; mode 1: only eta and ||r_dual|| (measurement).
 __global__ void __launch_bounds__(NT, 1) k_pdip_pre(PdipArgs A, int mode) {
+  barrier_init();
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -1337,6 +1400,7 @@ __global__ void __launch_bounds__(NT, 1) k_pdip_pre(PdipArgs A, int mode) {
 // ||r_t||), update.  Every block evaluates the same reduced scalars, so all
 // blocks take the same branches.
 __global__ void __launch_bounds__(NT, 1) k_pdip_post(PdipArgs A) {
+  barrier_init();
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -1454,7 +1518,7 @@ int coop_grid(qp_ctx* c, K kernel) {
   QP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, 0));
   QP_REQUIRE(per_sm > 0, QP_CUDA_ERROR, "cooperative kernel does not fit on an SM");
   if (per_sm > 2) per_sm = 2;
-  QP_REQUIRE(per_sm * c->num_sms <= 4096, QP_INVALID_ARG, "grid larger than the barrier flag array");
+  QP_REQUIRE(per_sm * c->num_sms <= 4096, QP_INVALID_ARG, "grid larger than the partial-sum array");
   return per_sm * c->num_sms;
 }
 
@@ -1729,10 +1793,13 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
         coop_launch(c, k, coop_grid(c, k), A);
       }
     } else if (mixed) {
-      auto k = k_pcg<float, float>;
+      auto k = k_pcg<float, void>;
+      coop_launch(c, k, coop_grid(c, k), A);
+    } else if (use_qtt) {
+      auto k = k_pcg<double, double>;
       coop_launch(c, k, coop_grid(c, k), A);
     } else {
-      auto k = k_pcg<double, double>;
+      auto k = k_pcg<double, void>;
       coop_launch(c, k, coop_grid(c, k), A);
     }
   }
