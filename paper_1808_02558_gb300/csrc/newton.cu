@@ -235,6 +235,42 @@ struct Operand {
   }
 };
 
+// Accumulate D_cb^T-weighted force and torque of up to NB incidences (codes
+// 2c + side, -1 = none); all record and operand loads are issued before use.
+template <int NB, class T, class X>
+__device__ __forceinline__ void gather_batch(const SysView<T>& s, const X& x, const int (&code)[NB], T& F0, T& F1,
+                                             T& F2, T& Q0, T& Q1, T& Q2) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (code[j] < 0) continue;
+    const int c = code[j] >> 1;
+    const long long row = (long long)s.slots * c;
+    T R[16];
+    load_rec(s.rec, c, R);
+    const T x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
+    T f0 = R[0] * x0 + R[3] * x1 + R[6] * x2;
+    T f1 = R[1] * x0 + R[4] * x1 + R[7] * x2;
+    T f2 = R[2] * x0 + R[5] * x1 + R[8] * x2;
+    const bool side_b = (code[j] & 1) != 0;
+    const T a0 = side_b ? R[12] : R[9], a1 = side_b ? R[13] : R[10], a2 = side_b ? R[14] : R[11];
+    const T sg = side_b ? T(1) : T(-1);
+    f0 *= sg;
+    f1 *= sg;
+    f2 *= sg;
+    F0 += f0;
+    F1 += f1;
+    F2 += f2;
+    Q0 += a1 * f2 - a2 * f1;
+    Q1 += a2 * f0 - a0 * f2;
+    Q2 += a0 * f1 - a1 * f0;
+  }
+}
+
+template <class T>
+constexpr int gather_nb() {
+  return sizeof(T) == 8 ? 2 : 4;  // batch size within the register budget
+}
+
 // w_b = M_b^-1 sum_{c in b} D_cb x_c   (force and torque of body b).
 // Incidences are taken in batches (4 in FP32, 2 in FP64): their codes first,
 // then all record and operand loads of the batch, so they are in flight together.
@@ -242,37 +278,103 @@ template <class T, class X>
 __device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int b) {
   T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
   const int e = __ldg(s.bptr + b + 1);
-  constexpr int NB = sizeof(T) == 8 ? 2 : 4;  // batch size within the register budget
+  constexpr int NB = gather_nb<T>();
   for (int k0 = __ldg(s.bptr + b); k0 < e; k0 += NB) {
     int code[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) code[j] = (k0 + j < e) ? __ldg(s.inc + k0 + j) : -1;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      if (code[j] < 0) continue;
-      const int c = code[j] >> 1;
-      const long long row = (long long)s.slots * c;
-      T R[16];
-      load_rec(s.rec, c, R);
-      const T x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
-      T f0 = R[0] * x0 + R[3] * x1 + R[6] * x2;
-      T f1 = R[1] * x0 + R[4] * x1 + R[7] * x2;
-      T f2 = R[2] * x0 + R[5] * x1 + R[8] * x2;
-      const bool side_b = (code[j] & 1) != 0;
-      const T a0 = side_b ? R[12] : R[9], a1 = side_b ? R[13] : R[10], a2 = side_b ? R[14] : R[11];
-      const T sg = side_b ? T(1) : T(-1);
-      f0 *= sg;
-      f1 *= sg;
-      f2 *= sg;
-      F0 += f0;
-      F1 += f1;
-      F2 += f2;
-      Q0 += a1 * f2 - a2 * f1;
-      Q1 += a2 * f0 - a0 * f2;
-      Q2 += a0 * f1 - a1 * f0;
-    }
+    gather_batch<NB>(s, x, code, F0, F1, F2, Q0, Q1, Q2);
   }
   const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+  T v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
+  store_w(s.w, b, v);
+}
+
+// Per-block work ranges and per-thread gather plan of a persistent Krylov
+// kernel, kept in shared memory for the whole launch.  Block g owns a
+// contiguous range of bodies holding an equal share (1/G) of the incidences,
+// and an equal contiguous share of the contacts, so that every SM gets the
+// same work in each operator pass.  Thread t of the block keeps the incidence
+// codes of its first body (up to PLAN_INC of them) and the body pairs of its
+// first PLAN_CON contacts, which removes the CSR and body-index loads, and
+// the load-to-load dependence they create, from every operator application.
+constexpr int PLAN_INC = 12;
+constexpr int PLAN_CON = 3;
+struct GatherPlan {
+  int code[PLAN_INC][NT];
+  int n[NT];                 // incidences of the thread's first body (0: none)
+  int ca[PLAN_CON][NT];
+  int cb[PLAN_CON][NT];
+  int b0, b1;                // bodies [b0, b1) of this block
+  int c0, c1;                // contacts [c0, c1) of this block
+};
+
+// first body whose incidence range ends above k (bptr is nondecreasing)
+__device__ __forceinline__ int body_at_incidence(const int* bptr, int M, long long k) {
+  int lo = 0, hi = M;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)__ldg(bptr + mid + 1) <= k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class T>
+__device__ void plan_fill(const SysView<T>& s, GatherPlan& pl) {
+  const int t = threadIdx.x;
+  const long long G = gridDim.x, g = blockIdx.x;
+  if (t == 0) {
+    const long long ninc = s.M > 0 ? (long long)__ldg(s.bptr + s.M) : 0;
+    pl.b0 = g == 0 ? 0 : body_at_incidence(s.bptr, s.M, ninc * g / G);
+    pl.b1 = g == G - 1 ? s.M : body_at_incidence(s.bptr, s.M, ninc * (g + 1) / G);
+    pl.c0 = (int)(s.Nc * g / G);
+    pl.c1 = (int)(s.Nc * (g + 1) / G);
+  }
+  __syncthreads();
+  int n = 0;
+  const int b = pl.b0 + t;
+  if (b < pl.b1) {
+    const int k0 = __ldg(s.bptr + b);
+    n = __ldg(s.bptr + b + 1) - k0;
+    for (int j = 0; j < PLAN_INC && j < n; ++j) pl.code[j][t] = __ldg(s.inc + k0 + j);
+  }
+  pl.n[t] = n;
+#pragma unroll
+  for (int k = 0; k < PLAN_CON; ++k) {
+    const int c = pl.c0 + t + k * (int)blockDim.x;
+    pl.ca[k][t] = c < pl.c1 ? __ldg(s.ca + c) : 0;
+    pl.cb[k][t] = c < pl.c1 ? __ldg(s.cb + c) : 0;
+  }
+  __syncthreads();
+}
+
+// body_gather for the thread's planned body b (= b0 + threadIdx.x).
+template <class T, class X>
+__device__ __forceinline__ void body_gather_planned(const SysView<T>& s, const X& x, const GatherPlan& pl, int b) {
+  const int t = threadIdx.x;
+  const int n = pl.n[t];
+  T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
+  constexpr int NB = gather_nb<T>();
+  const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+#pragma unroll
+  for (int k0 = 0; k0 < PLAN_INC; k0 += NB) {
+    if (k0 < n) {
+      int code[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) code[j] = (k0 + j < n) ? pl.code[k0 + j][t] : -1;
+      gather_batch<NB>(s, x, code, F0, F1, F2, Q0, Q1, Q2);
+    }
+  }
+  if (n > PLAN_INC) {
+    const int b0 = __ldg(s.bptr + b);
+    for (int k0 = b0 + PLAN_INC; k0 < b0 + n; k0 += NB) {
+      int code[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) code[j] = (k0 + j < b0 + n) ? __ldg(s.inc + k0 + j) : -1;
+      gather_batch<NB>(s, x, code, F0, F1, F2, Q0, Q1, Q2);
+    }
+  }
   T v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
   store_w(s.w, b, v);
 }
@@ -281,9 +383,9 @@ __device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int
 // If xout is set, the operand value of row i is also stored there (the
 // materialised search direction).
 template <class T, class X>
-__device__ __forceinline__ T contact_apply(const SysView<T>& s, const X& x, T* y, int c, T* xout = nullptr) {
+__device__ __forceinline__ T contact_apply_ab(const SysView<T>& s, const X& x, T* y, int c, int a, int b,
+                                              T* xout = nullptr) {
   const long long n = s.Nc;
-  const int a = __ldg(s.ca + c), b = __ldg(s.cb + c);
   T R[16];
   load_rec(s.rec, c, R);
   T wb[6];
@@ -327,6 +429,33 @@ __device__ __forceinline__ T contact_apply(const SysView<T>& s, const X& x, T* y
     dot += x3 * x3;
   }
   return dot;
+}
+
+template <class T, class X>
+__device__ __forceinline__ T contact_apply(const SysView<T>& s, const X& x, T* y, int c, T* xout = nullptr) {
+  return contact_apply_ab(s, x, y, c, __ldg(s.ca + c), __ldg(s.cb + c), xout);
+}
+
+// Operator passes of a persistent kernel with a gather plan: w for the
+// block's bodies, then y for the block's contacts (returns the thread's share
+// of x . y).
+template <class T, class X>
+__device__ __forceinline__ void gather_all(const SysView<T>& s, const X& x, const GatherPlan& pl) {
+  const int b = pl.b0 + threadIdx.x;
+  if (b < pl.b1) body_gather_planned(s, x, pl, b);
+  for (int bd = b + blockDim.x; bd < pl.b1; bd += blockDim.x) body_gather(s, x, bd);
+}
+template <class T, class X>
+__device__ __forceinline__ T apply_all(const SysView<T>& s, const X& x, T* y, const GatherPlan& pl, T* xout) {
+  T acc = 0;
+  const int c = pl.c0 + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < PLAN_CON; ++k) {
+    const int ck = c + k * (int)blockDim.x;
+    if (ck < pl.c1) acc += contact_apply_ab(s, x, y, ck, pl.ca[k][threadIdx.x], pl.cb[k][threadIdx.x], xout);
+  }
+  for (int ck = c + PLAN_CON * (int)blockDim.x; ck < pl.c1; ck += blockDim.x) acc += contact_apply(s, x, y, ck, xout);
+  return acc;
 }
 
 template <class T>
@@ -473,7 +602,7 @@ __device__ __forceinline__ bool qtt_precond_if(const PcgArgs& A, const T* in, T*
 }
 
 template <class T, class TC>
-__device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
+__device__ int inner_pcg(const PcgArgs& A, const GatherPlan& pl, double tol, int maxit, int& iters) {
   const SysView<T>& s = sys_of<T>(A);
   T* b = static_cast<T*>(A.b);
   T* e = static_cast<T*>(A.e);
@@ -523,10 +652,9 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
     if (!(rz > 0.0)) return 2;
     const Operand<T> dir{z, it == 0 ? nullptr : pold, (T)beta};
     // q = S p_k
-    for (int bd = (int)tid; bd < s.M; bd += (int)gsz) body_gather(s, dir, bd);
+    gather_all(s, dir, pl);
     if (!grid_barrier(A.ctl, nb)) return -1;
-    T a2[1] = {};
-    for (int c = (int)tid; c < s.Nc; c += (int)gsz) a2[0] += contact_apply(s, dir, q, c, pnew);
+    T a2[1] = {apply_all(s, dir, q, pl, pnew)};
     block_partials<1>(a2, A.partial, 2);
     double t2[1];
     if (!grid_barrier_total<1>(A.ctl, nb, A.partial, 2, t2)) return -1;
@@ -547,17 +675,37 @@ __device__ int inner_pcg(const PcgArgs& A, double tol, int maxit, int& iters) {
         float4* R4 = reinterpret_cast<float4*>(r);
         float4* Z4 = reinterpret_cast<float4*>(z);
         const float al = (float)alpha;
-        for (long long i = tid; i < n4; i += gsz) {
-          const float4 pv = P4[i], qv = Q4[i], dv = D4[i];
-          float4 ev = E4[i], rv = R4[i];
-          ev.x += al * pv.x; ev.y += al * pv.y; ev.z += al * pv.z; ev.w += al * pv.w;
-          rv.x -= al * qv.x; rv.y -= al * qv.y; rv.z -= al * qv.z; rv.w -= al * qv.w;
-          const float4 zv = make_float4(dv.x * rv.x, dv.y * rv.y, dv.z * rv.z, dv.w * rv.w);
-          E4[i] = ev;
-          R4[i] = rv;
-          Z4[i] = zv;
-          a3[0] += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
-          a3[1] += rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
+        // the block's equal share of the float4 rows; two float4 per thread
+        // and pass, all loads of the pass before any store
+        const long long u0 = n4 * blockIdx.x / gridDim.x, u1 = n4 * (blockIdx.x + 1) / gridDim.x;
+        const long long bs = blockDim.x;
+        for (long long i0 = u0 + threadIdx.x; i0 < u1; i0 += 2 * bs) {
+          float4 pv[2], qv[2], dv[2], ev[2], rv[2];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const long long i = i0 + j * bs;
+            if (i < u1) {
+              pv[j] = P4[i];
+              qv[j] = Q4[i];
+              dv[j] = D4[i];
+              ev[j] = E4[i];
+              rv[j] = R4[i];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const long long i = i0 + j * bs;
+            if (i >= u1) break;
+            float4 e4 = ev[j], r4 = rv[j];
+            e4.x += al * pv[j].x; e4.y += al * pv[j].y; e4.z += al * pv[j].z; e4.w += al * pv[j].w;
+            r4.x -= al * qv[j].x; r4.y -= al * qv[j].y; r4.z -= al * qv[j].z; r4.w -= al * qv[j].w;
+            const float4 z4 = make_float4(dv[j].x * r4.x, dv[j].y * r4.y, dv[j].z * r4.z, dv[j].w * r4.w);
+            E4[i] = e4;
+            R4[i] = r4;
+            Z4[i] = z4;
+            a3[0] += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
+            a3[1] += r4.x * z4.x + r4.y * z4.y + r4.z * z4.z + r4.w * z4.w;
+          }
         }
         for (long long i = (n4 << 2) + tid; i < nrow; i += gsz) {
           e[i] += (T)alpha * pnew[i];
@@ -750,7 +898,9 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
 // FP64 outer refinement: r64 = rhs - S x; inner solve on r64/||r64||; x += ...
 template <class T, class TC>
 __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
+  __shared__ GatherPlan pl;
   barrier_init();
+  plan_fill(A.s64, pl);
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -784,9 +934,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
           rr[0] += A.rhs[i] * A.rhs[i];
         }
       } else {
-        for (int bd = (int)tid; bd < s64.M; bd += (int)gsz) body_gather(s64, plain<double>(A.x), bd);
+        gather_all(s64, plain<double>(A.x), pl);
         if (!grid_barrier(A.ctl, nb)) return;
-        for (int c = (int)tid; c < s64.Nc; c += (int)gsz) contact_apply(s64, plain<double>(A.x), A.q64, c);
+        apply_all(s64, plain<double>(A.x), A.q64, pl, (double*)nullptr);
         if (!grid_barrier(A.ctl, nb)) return;
         for (long long i = tid; i < A.nrow; i += gsz) {
           double ri = A.rhs[i] - A.q64[i];
@@ -810,7 +960,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
       for (long long i = tid; i < A.nrow; i += gsz) b[i] = (T)(A.r64[i] * inv);
       if (!grid_barrier(A.ctl, nb)) return;
       int st = A.krylov == QP_BICGSTAB ? inner_bicgstab<T, TC>(A, A.inner_tol, A.maxit - iters, iters)
-                                       : inner_pcg<T, TC>(A, A.inner_tol, A.maxit - iters, iters);
+                                       : inner_pcg<T, TC>(A, pl, A.inner_tol, A.maxit - iters, iters);
       if (st < 0) return;
       for (long long i = tid; i < A.nrow; i += gsz) A.x[i] += rn * (double)e[i];
       if (!grid_barrier(A.ctl, nb)) return;
@@ -1689,7 +1839,10 @@ static void solve_fused(qp_ctx* c, const double* rhs, double* dx, const qp_solve
   A.x = dx;
   A.r64 = static_cast<double*>(c->v64[5].ensure(P * sizeof(double)));
   A.q64 = static_cast<double*>(c->v64[6].ensure(P * sizeof(double)));
-  A.pool = (mixed ? c->v32[0] : c->scratch[0]).ensure(16 * P * es);  // pipe + state records
+  // pipe + state records in a buffer of their own: the classic solver that may
+  // run after a failed fused solve holds pointers into v32 / scratch, which a
+  // reallocation here would invalidate
+  A.pool = c->fused_pool.ensure(16 * P * es);
   A.dinv = mixed ? (const void*)c->dinv32.p : (const void*)c->dinv.p;
   A.tol = o->tol;
   A.inner_tol = mixed ? (o->inner_tol > 0 ? o->inner_tol : 1e-4) : (o->inner_tol > 0 ? o->inner_tol : o->tol);

@@ -125,6 +125,28 @@ def test_solve_mixed_precision_full_size(ctx):
     assert abs(res - stats.rel_res) <= 1e-9
 
 
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_failed_pipelined_solve_falls_back_on_fresh_context(ctx, mixed):
+    """The first solve of a fresh context runs the pipelined kernel (small
+    system), fails on an unattainable tolerance and is redone by the classic
+    kernel, whose work vectors must survive the pipelined solver's allocations."""
+    pb = Problem(ctx, scene_for("pile8", 2))
+    g, lam = interior_point(pb, 1)
+    gd, ld, st = pb.state(g, lam)
+    rhs = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    pb.ctx.newton_rhs(st, rhs)
+    dx = torch.empty_like(rhs)
+    opts = pb.ctx.solve_opts(tol=1e-30, maxit=40, mixed=mixed, inner_tol=1e-3 if mixed else 0.0, max_outer=2)
+    stats = pb.ctx.newton_solve(st, rhs, dx, opts)
+    assert stats.status in (binding.QP_NOT_CONVERGED, binding.QP_BREAKDOWN)
+    assert torch.isfinite(dx).all().item()
+    opts = pb.ctx.solve_opts(tol=1e-10, maxit=50000, mixed=mixed, inner_tol=1e-3 if mixed else 0.0, max_outer=60)
+    stats = pb.ctx.newton_solve(st, rhs, dx, opts, allow=())
+    S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+    b = pb.unpad(to_np(rhs))
+    assert np.linalg.norm(b - S @ pb.unpad(to_np(dx))) <= 1.05e-10 * np.linalg.norm(b)
+
+
 def test_solve_zero_rhs(pile8):
     g, lam = pile8.iters[0]
     gd, ld, st = pile8.state(g, lam)
