@@ -125,12 +125,16 @@ int newton_apply(qp_ctx_t ctx, const qp_state* st, const void* x, void* y, qp_dt
  * + (1/t) sum_i grad f_i / f_i (padded, dummies 0).                         */
 int newton_rhs(qp_ctx_t ctx, const qp_state* st, double* rhs);
 
-typedef enum { QP_JACOBI_PCG = 0, QP_QTT_PCG = 1 } qp_precond;
+/* QP_QTT_DIRECT uses X as an approximate direct solver (Sec. 3.3): each
+ * refinement step applies X to the FP64 residual, dx += X (rhs - S dx), until
+ * tol; it converges when the spectral radius of I - S X is below 1.  max_outer
+ * caps the refinements (default 100).                                       */
+typedef enum { QP_JACOBI_PCG = 0, QP_QTT_PCG = 1, QP_QTT_DIRECT = 2 } qp_precond;
 typedef enum { QP_CG = 0, QP_BICGSTAB = 1 } qp_krylov;
 
 typedef struct {
   qp_precond precond; /* Jacobi (diag S) or the QTT approximate inverse        */
-  qtt_t X;            /* QP_QTT_PCG: preconditioner (approximate S^-1)         */
+  qtt_t X;            /* QP_QTT_PCG / QP_QTT_DIRECT: approximate S^-1          */
   double tol;         /* stop at ||rhs - S dx||_2 <= tol ||rhs||_2             */
   int maxit;          /* Krylov iteration cap (total inner iterations)         */
   int mixed;          /* 1: FP32 inner PCG + FP64 outer refinement             */
@@ -195,6 +199,18 @@ int pdip_step(qp_ctx_t ctx, qp_state* st, const qp_pdip_opts* opts, qp_pdip_stat
 
 /* Surrogate gap and dual residual norm at st (host scalars).                */
 int pdip_measure(qp_ctx_t ctx, const qp_state* st, double* eta_host, double* r_dual_host);
+
+/* The PDIP loop (Sec. 2.4; Boyd and Vandenberghe, Alg. 11.2): starting from
+ * st, measure eta and ||r_dual||; while eta > gap_tol or ||r_dual|| > dual_tol
+ * and fewer than max_iter steps were taken, run pdip_step.  st is updated in
+ * place and holds the last iterate in every case.  A Krylov solve that stops
+ * at its iteration cap (QP_NOT_CONVERGED) gives an inexact Newton step and the
+ * loop goes on; any other step error ends the loop and is returned.
+ * Returns QP_OK when both tolerances are met, QP_NOT_CONVERGED after max_iter
+ * steps.  stats (may be NULL): the last step's statistics, with eta and r_dual
+ * replaced by the final measurement; iters_host (may be NULL): steps taken.  */
+int pdip_solve(qp_ctx_t ctx, qp_state* st, const qp_pdip_opts* opts, double gap_tol, double dual_tol, int max_iter,
+               qp_pdip_stats* stats, int* iters_host);
 
 /* ---- QTT matrices (Sec. 3.1-3.2) --------------------------------------- */
 

@@ -19,12 +19,12 @@ LIB_PATH = os.path.join(HERE, "libqttpdip.so")
 QP_OK, QP_INVALID_ARG, QP_OOM, QP_CUDA_ERROR = 0, -1, -2, -3
 QP_NOT_CONVERGED, QP_BREAKDOWN, QP_LINESEARCH_FAIL, QP_TIMEOUT, QP_NOT_READY = -4, -5, -6, -7, -8
 QP_F64, QP_F32, QP_BF16 = 0, 1, 2
-QP_JACOBI_PCG, QP_QTT_PCG = 0, 1
+QP_JACOBI_PCG, QP_QTT_PCG, QP_QTT_DIRECT = 0, 1, 2
 QP_CG, QP_BICGSTAB = 0, 1
 QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
-           "newton_apply", "newton_rhs", "newton_solve", "pdip_step", "pdip_measure", "qtt_from_host",
+           "newton_apply", "newton_rhs", "newton_solve", "pdip_step", "pdip_measure", "pdip_solve", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "newton_solve": (i, [vp, C.POINTER(State), vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
         "pdip_step": (i, [vp, C.POINTER(State), C.POINTER(PdipOpts), C.POINTER(PdipStats)]),
         "pdip_measure": (i, [vp, C.POINTER(State), C.POINTER(d), C.POINTER(d)]),
+        "pdip_solve": (i, [vp, C.POINTER(State), C.POINTER(PdipOpts), d, d, i, C.POINTER(PdipStats), C.POINTER(i)]),
         "qtt_from_host": (i, [vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(vp)]),
         "qtt_free": (i, [vp, vp]),
         "qtt_get_dims": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
@@ -265,6 +266,15 @@ class Context:
         stats = PdipStats()
         self._check(self.lib.pdip_step(self.h, C.byref(st), C.byref(opts), C.byref(stats)), "pdip_step", allow=allow)
         return stats
+
+    def pdip_solve(self, st: State, opts: PdipOpts, gap_tol=1e-8, dual_tol=1e-8, max_iter=200,
+                   allow=(QP_NOT_CONVERGED,)):
+        """PDIP loop to the given tolerances; returns (stats, steps taken)."""
+        stats = PdipStats()
+        n = C.c_int(0)
+        self._check(self.lib.pdip_solve(self.h, C.byref(st), C.byref(opts), float(gap_tol), float(dual_tol),
+                                        int(max_iter), C.byref(stats), C.byref(n)), "pdip_solve", allow=allow)
+        return stats, n.value
 
     def pdip_measure(self, st: State):
         eta, rd = C.c_double(), C.c_double()

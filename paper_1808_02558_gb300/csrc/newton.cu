@@ -101,80 +101,104 @@ __device__ __forceinline__ double warp_min(double v) {
 }
 
 // Block-reduce n values (sum) and store them as this block's partials.  The
-// per-thread and per-warp sums are taken in the accumulator type V (float in
-// the FP32 inner solves, where FP64 arithmetic is a slow pipe, double
-// elsewhere); warps are combined in double.
-template <int N, class V>
+// per-thread and per-warp sums are taken in the accumulator type V, the
+// cross-warp sum and the stored partial in the reduction type R: float in
+// the FP32 inner solves, double elsewhere.  FP64 arithmetic is a narrow,
+// long-latency pipe on this part, so FP64 sums are kept to short trees in one
+// warp.  A float partial of slot s sits in the first half of double slot s.
+template <class R>
+__device__ __forceinline__ R* partial_slot(double* partial, int b, int slot) {
+  return reinterpret_cast<R*>(partial + (size_t)b * NRED + slot);
+}
+template <class R>
+__device__ __forceinline__ R load_partial(const double* partial, int b, int slot) {
+  return *reinterpret_cast<volatile const R*>(partial + (size_t)b * NRED + slot);
+}
+
+template <int N, class V, class R = double>
 __device__ void block_partials(V (&v)[N], double* partial, int slot0, bool is_min = false) {
-  __shared__ double sm[N][NWMAX];
+  __shared__ R sm[N][NWMAX];
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int k = 0; k < N; ++k) {
-    double x = is_min ? warp_min((double)v[k]) : (double)warp_sum(v[k]);
-    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = x;
+    if (is_min) {
+      const double x = warp_min((double)v[k]);
+      if (lane == 0) sm[k][threadIdx.x >> 5] = (R)x;
+    } else {
+      const V x = warp_sum(v[k]);
+      if (lane == 0) sm[k][threadIdx.x >> 5] = (R)x;
+    }
   }
   __syncthreads();
-  if (threadIdx.x < N) {
-    double x = sm[threadIdx.x][0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = is_min ? fmin(x, sm[threadIdx.x][w]) : x + sm[threadIdx.x][w];
-    partial[(size_t)blockIdx.x * NRED + slot0 + threadIdx.x] = x;
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < N; ++k) {
+      R x;
+      if (is_min) {
+        x = lane < nw ? sm[k][lane] : R(1e300);
+        x = (R)warp_min((double)x);
+      } else {
+        x = lane < nw ? sm[k][lane] : R(0);
+        x = warp_sum(x);
+      }
+      if (lane == 0) *partial_slot<R>(partial, blockIdx.x, slot0 + k) = x;
+    }
   }
   __syncthreads();
 }
 
-// Sum (or min) of one partial slot over all blocks, same value in every block.
+// Sum (or min) of one partial slot over all blocks, same value in every block
+// (warp 0 reduces, in a fixed order).
 __device__ double grid_total(const double* partial, int slot, bool is_min = false) {
-  __shared__ double sm[NWMAX];
   __shared__ double res;
-  double x = is_min ? 1e300 : 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    double y = *(volatile const double*)&partial[(size_t)b * NRED + slot];
-    x = is_min ? fmin(x, y) : x + y;
-  }
-  x = is_min ? warp_min(x) : warp_sum(x);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = sm[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = is_min ? fmin(t, sm[w]) : t + sm[w];
-    res = t;
+  if (threadIdx.x < 32) {
+    double x = is_min ? 1e300 : 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+      const double y = *(volatile const double*)&partial[(size_t)b * NRED + slot];
+      x = is_min ? fmin(x, y) : x + y;
+    }
+    x = is_min ? warp_min(x) : warp_sum(x);
+    if (threadIdx.x == 0) res = x;
   }
   __syncthreads();
-  double out = res;
+  const double out = res;
   __syncthreads();
   return out;
 }
 
 // Grid barrier that also forms the totals of K consecutive partial slots
-// (written by block_partials before the barrier) in the same pass over the
-// blocks.  Every block adds the same values in the same order, so all blocks
-// obtain bit-identical totals.
-template <int K>
-__device__ bool grid_barrier_total(DevCtl* ctl, unsigned nblocks, const double* partial, int slot,
-                                   double (&out)[K], long long budget = BARRIER_BUDGET) {
-  __shared__ double sm[K][NWMAX];
-  __shared__ double res[K];
+// (written by block_partials before the barrier).  Warp 0 adds the blocks'
+// partials in a fixed order, so all blocks obtain bit-identical totals; then
+// thread 0 runs `scal` on the totals (the scalar recurrences of a Krylov
+// method, written to shared memory), so that FP64 scalar work is done once per
+// block rather than by every thread.  Shared results are visible to the whole
+// block when this returns and stay valid until the next barrier call.
+struct NoScal {
+  template <class R>
+  __device__ void operator()(const R*) const {}
+};
+
+template <int K, class R = double, class F = NoScal>
+__device__ bool grid_barrier_total(DevCtl* ctl, unsigned nblocks, const double* partial, int slot, R (&out)[K],
+                                   F scal = F(), long long budget = BARRIER_BUDGET) {
+  __shared__ R res[K];
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) ok = barrier_arrive_wait(ctl, nblocks, budget) ? 1 : 0;
   __syncthreads();
   const bool good = ok != 0;
-  double x[K];
-  for (int k = 0; k < K; ++k) x[k] = 0.0;
-  if (good)
-    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
-      for (int k = 0; k < K; ++k) x[k] += *(volatile const double*)&partial[(size_t)b * NRED + slot + k];
-  for (int k = 0; k < K; ++k) {
-    const double v = warp_sum(x[k]);
-    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < K) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[threadIdx.x][w];
-    res[threadIdx.x] = t;
+  if (threadIdx.x < 32) {
+    R x[K];
+    for (int k = 0; k < K; ++k) x[k] = R(0);
+    if (good)
+      for (unsigned b = threadIdx.x; b < nblocks; b += 32)
+        for (int k = 0; k < K; ++k) x[k] += load_partial<R>(partial, b, slot + k);
+    for (int k = 0; k < K; ++k) x[k] = warp_sum(x[k]);
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < K; ++k) res[k] = x[k];
+      if (good) scal(res);
+    }
   }
   __syncthreads();
   for (int k = 0; k < K; ++k) out[k] = res[k];
-  __syncthreads();
   return good;
 }
 
@@ -274,11 +298,10 @@ constexpr int gather_nb() {
 // w_b = M_b^-1 sum_{c in b} D_cb x_c   (force and torque of body b).
 // Incidences are taken in batches (4 in FP32, 2 in FP64): their codes first,
 // then all record and operand loads of the batch, so they are in flight together.
-template <class T, class X>
+template <class T, class X, int NB = gather_nb<T>()>
 __device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int b) {
   T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
   const int e = __ldg(s.bptr + b + 1);
-  constexpr int NB = gather_nb<T>();
   for (int k0 = __ldg(s.bptr + b); k0 < e; k0 += NB) {
     int code[NB];
 #pragma unroll
@@ -350,12 +373,11 @@ __device__ void plan_fill(const SysView<T>& s, GatherPlan& pl) {
 }
 
 // body_gather for the thread's planned body b (= b0 + threadIdx.x).
-template <class T, class X>
+template <class T, class X, int NB = gather_nb<T>()>
 __device__ __forceinline__ void body_gather_planned(const SysView<T>& s, const X& x, const GatherPlan& pl, int b) {
   const int t = threadIdx.x;
   const int n = pl.n[t];
   T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
-  constexpr int NB = gather_nb<T>();
   const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
 #pragma unroll
   for (int k0 = 0; k0 < PLAN_INC; k0 += NB) {
@@ -439,11 +461,11 @@ __device__ __forceinline__ T contact_apply(const SysView<T>& s, const X& x, T* y
 // Operator passes of a persistent kernel with a gather plan: w for the
 // block's bodies, then y for the block's contacts (returns the thread's share
 // of x . y).
-template <class T, class X>
+template <class T, class X, int NB = gather_nb<T>()>
 __device__ __forceinline__ void gather_all(const SysView<T>& s, const X& x, const GatherPlan& pl) {
   const int b = pl.b0 + threadIdx.x;
-  if (b < pl.b1) body_gather_planned(s, x, pl, b);
-  for (int bd = b + blockDim.x; bd < pl.b1; bd += blockDim.x) body_gather(s, x, bd);
+  if (b < pl.b1) body_gather_planned<T, X, NB>(s, x, pl, b);
+  for (int bd = b + blockDim.x; bd < pl.b1; bd += blockDim.x) body_gather<T, X, NB>(s, x, bd);
 }
 template <class T, class X>
 __device__ __forceinline__ T apply_all(const SysView<T>& s, const X& x, T* y, const GatherPlan& pl, T* xout) {
@@ -539,6 +561,7 @@ struct PcgArgs {
   void* qw1;
   void* xb;                 // BiCGSTAB vectors (type T), 5 * P
   int krylov;               // QP_CG or QP_BICGSTAB
+  int direct;               // QTT direct mode: the inner solve is one application of X
   double tol, inner_tol;
   int maxit, max_outer;
   DevCtl* ctl;
@@ -630,37 +653,42 @@ __device__ int inner_pcg(const PcgArgs& A, const GatherPlan& pl, double tol, int
       acc[1] += bi * zi;
     }
   }
-  block_partials<2>(acc, A.partial, 0);
-  double t0[2];
-  if (!grid_barrier_total<2>(A.ctl, nb, A.partial, 0, t0)) return -1;
-  const double bb = t0[0];
-  double rz = t0[1];
-  if (bb == 0.0) return 0;
+  // reductions and scalar recurrences in T (float in the FP32 inner solve)
+  block_partials<2, T, T>(acc, A.partial, 0);
+  T t0[2];
+  if (!grid_barrier_total<2, T>(A.ctl, nb, A.partial, 0, t0)) return -1;
+  const T bb = t0[0];
+  T rz = t0[1];
+  if (bb == T(0)) return 0;
   if ((kQtt<TC> && A.use_qtt)) {
     if (!qtt_precond_if<T, TC>(A, r, z)) return -1;
     T a1[1] = {};
     for (long long i = tid; i < nrow; i += gsz) a1[0] += r[i] * z[i];
-    block_partials<1>(a1, A.partial, 1);
-    if (!grid_barrier(A.ctl, nb)) return -1;
-    rz = grid_total(A.partial, 1);
+    block_partials<1, T, T>(a1, A.partial, 1);
+    T t1[1];
+    if (!grid_barrier_total<1, T>(A.ctl, nb, A.partial, 1, t1)) return -1;
+    rz = t1[0];
   }
-  const double stop = tol * tol * bb;
+  const T stop = (T)(tol * tol) * bb;
   T* pold = pa;   // p_{k-1} (unused while beta == 0)
   T* pnew = pb;   // p_k, written by the contact pass
-  double beta = 0.0;
+  T beta = 0;
   for (int it = 0; it < maxit; ++it) {
-    if (!(rz > 0.0)) return 2;
-    const Operand<T> dir{z, it == 0 ? nullptr : pold, (T)beta};
+    if (!(rz > T(0))) return 2;
+    const Operand<T> dir{z, it == 0 ? nullptr : pold, beta};
     // q = S p_k
     gather_all(s, dir, pl);
     if (!grid_barrier(A.ctl, nb)) return -1;
     T a2[1] = {apply_all(s, dir, q, pl, pnew)};
-    block_partials<1>(a2, A.partial, 2);
-    double t2[1];
-    if (!grid_barrier_total<1>(A.ctl, nb, A.partial, 2, t2)) return -1;
-    const double pq = t2[0];
-    if (!(pq > 0.0)) return 2;
-    const double alpha = rz / pq;
+    block_partials<1, T, T>(a2, A.partial, 2);
+    T t2[1];
+    __shared__ T s_alpha;
+    if (!grid_barrier_total<1, T>(A.ctl, nb, A.partial, 2, t2,
+                                  [&](const T* t) { s_alpha = t[0] > T(0) ? rz / t[0] : T(0); }))
+      return -1;
+    const T pq = t2[0];
+    if (!(pq > T(0))) return 2;
+    const T alpha = s_alpha;
     T a3[2] = {};
     bool updated = false;
     if constexpr (sizeof(T) == 4) {
@@ -750,24 +778,28 @@ __device__ int inner_pcg(const PcgArgs& A, const GatherPlan& pl, double tol, int
       }
     }
     }
-    block_partials<2>(a3, A.partial, 3);
-    double t3[2];
-    if (!grid_barrier_total<2>(A.ctl, nb, A.partial, 3, t3)) return -1;
+    block_partials<2, T, T>(a3, A.partial, 3);
+    T t3[2];
+    __shared__ T s_beta;
+    if (!grid_barrier_total<2, T>(A.ctl, nb, A.partial, 3, t3, [&](const T* t) { s_beta = t[1] / rz; }))
+      return -1;
     ++iters;
-    const double rr = t3[0];
-    double rz_new;
+    const T rr = t3[0];
+    T rz_new;
     if (rr <= stop) return 0;
     if ((kQtt<TC> && A.use_qtt)) {
       if (!qtt_precond_if<T, TC>(A, r, z)) return -1;
       T a4[1] = {};
       for (long long i = tid; i < nrow; i += gsz) a4[0] += r[i] * z[i];
-      block_partials<1>(a4, A.partial, 5);
-      if (!grid_barrier(A.ctl, nb)) return -1;
-      rz_new = grid_total(A.partial, 5);
+      block_partials<1, T, T>(a4, A.partial, 5);
+      T t4[1];
+      if (!grid_barrier_total<1, T>(A.ctl, nb, A.partial, 5, t4, [&](const T* t) { s_beta = t[0] / rz; }))
+        return -1;
+      rz_new = t4[0];
     } else {
       rz_new = t3[1];
     }
-    beta = rz_new / rz;
+    beta = s_beta;
     rz = rz_new;
     T* t = pold;
     pold = pnew;
@@ -916,6 +948,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
   for (long long i = A.nrow + tid; i < A.P; i += gsz) {
     static_cast<T*>(A.r)[i] = 0;
     static_cast<T*>(A.z)[i] = 0;
+    b[i] = 0;
   }
   block_partials<1>(a0, A.partial, 6);
   if (!grid_barrier(A.ctl, nb)) return;
@@ -959,8 +992,14 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
       const double inv = 1.0 / rn;
       for (long long i = tid; i < A.nrow; i += gsz) b[i] = (T)(A.r64[i] * inv);
       if (!grid_barrier(A.ctl, nb)) return;
-      int st = A.krylov == QP_BICGSTAB ? inner_bicgstab<T, TC>(A, A.inner_tol, A.maxit - iters, iters)
-                                       : inner_pcg<T, TC>(A, pl, A.inner_tol, A.maxit - iters, iters);
+      int st;
+      if (A.direct) {
+        // refinement with the approximate inverse: e = X b
+        if (!qtt_precond_if<T, TC>(A, b, static_cast<T*>(A.e))) return;
+        ++iters;
+        st = 0;
+      } else if (A.krylov == QP_BICGSTAB) st = inner_bicgstab<T, TC>(A, A.inner_tol, A.maxit - iters, iters);
+      else st = inner_pcg<T, TC>(A, pl, A.inner_tol, A.maxit - iters, iters);
       if (st < 0) return;
       for (long long i = tid; i < A.nrow; i += gsz) A.x[i] += rn * (double)e[i];
       if (!grid_barrier(A.ctl, nb)) return;
@@ -1270,12 +1309,13 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
   }
   // w0 = S M^-1 b into the n[1] slot of each row (no one reads n[1] in this phase)
   fused_apply(s, A.pt, OpRhs<T>{pr, sr}, pr + 3, 8, wl);
-  block_partials<3>(acc, A.partial, 0);
-  double tot[3];
-  if (!grid_barrier_total<3>(A.ctl, nb, A.partial, 0, tot)) return -1;
-  double gamma = tot[0];
-  const double bb = tot[1];
-  if (bb == 0.0) return 0;
+  // reductions and scalar recurrences in T (float in the FP32 inner solve)
+  block_partials<3, T, T>(acc, A.partial, 0);
+  T tot[3];
+  if (!grid_barrier_total<3, T>(A.ctl, nb, A.partial, 0, tot)) return -1;
+  T gamma = tot[0];
+  const T bb = tot[1];
+  if (bb == T(0)) return 0;
   // phase 0: w[0] <- n[1] (own rows); n0 = S M^-1 w0 into n[0]; delta0 = (w0, u0)
   T acc1[3] = {};
   for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -1286,15 +1326,15 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
   __syncthreads();
   // other blocks read w0 of our rows through n[1]: use that slot as the operand
   fused_apply(s, A.pt, OpW<T>{pr, 3}, pr + 2, 8, wl);
-  block_partials<3>(acc1, A.partial, 3);
-  if (!grid_barrier_total<3>(A.ctl, nb, A.partial, 3, tot)) return -1;
-  double delta = tot[0];
-  if (!(gamma > 0.0) || !(delta > 0.0)) return 2;
-  double alpha = gamma / delta, beta = 0.0;
-  const double stop = tol * tol * bb;
+  block_partials<3, T, T>(acc1, A.partial, 3);
+  if (!grid_barrier_total<3, T>(A.ctl, nb, A.partial, 3, tot)) return -1;
+  const T delta = tot[0];
+  if (!(gamma > T(0)) || !(delta > T(0))) return 2;
+  T alpha = gamma / delta, beta = 0;
+  const T stop = (T)(tol * tol) * bb;
   int cur = 0;  // w[cur] = w_i, n[cur] = n_i, z[cur ^ 1] = z_{i-1}
   for (int it = 0; it < maxit; ++it) {
-    const T a = (T)alpha, bt = (T)beta;
+    const T a = alpha, bt = beta;
     const int nxt = cur ^ 1;
     T d3[3] = {};
 #pragma unroll 2
@@ -1327,17 +1367,32 @@ __device__ int inner_pcg_fused(const FusedArgs& A, double tol, int maxit, int& i
     // one barrier per iteration: alternate the partial-sum slots so that a block
     // already in the next iteration never overwrites sums still being read
     const int sl = 6 + 3 * (it & 1);
-    block_partials<3>(d3, A.partial, sl);
-    if (!grid_barrier_total<3>(A.ctl, nb, A.partial, sl, tot)) return -1;
+    block_partials<3, T, T>(d3, A.partial, sl);
+    // thread 0: next (alpha, beta) and the exit code (-2: continue)
+    __shared__ T s_ab[2];
+    __shared__ int s_exit;
+    if (!grid_barrier_total<3, T>(A.ctl, nb, A.partial, sl, tot, [&](const T* t) {
+          const T gnew = t[0], dnew = t[1], rr = t[2];
+          int ex = -2;
+          T al = alpha, be = beta;
+          if (rr <= stop) ex = 0;
+          else if (!(gnew > T(0))) ex = 2;
+          else {
+            be = gnew / gamma;
+            const T den = dnew - be * gnew / alpha;
+            if (!(den > T(0))) ex = 2;
+            else al = gnew / den;
+          }
+          s_ab[0] = al;
+          s_ab[1] = be;
+          s_exit = ex;
+        }))
+      return -1;
     ++iters;
-    const double gnew = tot[0], dnew = tot[1], rr = tot[2];
-    if (rr <= stop) return 0;
-    if (!(gnew > 0.0)) return 2;
-    beta = gnew / gamma;
-    const double den = dnew - beta * gnew / alpha;
-    if (!(den > 0.0)) return 2;
-    alpha = gnew / den;
-    gamma = gnew;
+    if (s_exit != -2) return s_exit;
+    alpha = s_ab[0];
+    beta = s_ab[1];
+    gamma = tot[0];
     cur = nxt;
   }
   return 1;
@@ -1862,7 +1917,9 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   QP_REQUIRE(o, QP_INVALID_ARG, "newton_solve: null options");
   QP_REQUIRE(o->tol > 0 && o->maxit > 0, QP_INVALID_ARG, "newton_solve: tol > 0 and maxit > 0 required");
   const bool mixed = o->mixed != 0;
-  const bool use_qtt = o->precond == QP_QTT_PCG;
+  QP_REQUIRE(o->precond == QP_JACOBI_PCG || o->precond == QP_QTT_PCG || o->precond == QP_QTT_DIRECT,
+             QP_INVALID_ARG, "newton_solve: unknown preconditioner");
+  const bool use_qtt = o->precond == QP_QTT_PCG || o->precond == QP_QTT_DIRECT;
   QP_REQUIRE(!use_qtt || o->X, QP_INVALID_ARG, "newton_solve: QTT preconditioner requires X");
   const size_t P = (size_t)c->P;
   PcgArgs A;
@@ -1887,6 +1944,7 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   A.qtt_scaled = (use_qtt && o->X->scaled) ? 1 : 0;
   A.qw0 = A.qw1 = nullptr;
   A.krylov = o->krylov == QP_BICGSTAB ? QP_BICGSTAB : QP_CG;
+  A.direct = o->precond == QP_QTT_DIRECT ? 1 : 0;
   A.xb = A.krylov == QP_BICGSTAB ? c->dm[12].ensure(5 * P * es) : nullptr;
   qp_dtype cdt = QP_F64;
   if (use_qtt) {
@@ -1910,7 +1968,7 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   A.tol = o->tol;
   A.inner_tol = mixed ? (o->inner_tol > 0 ? o->inner_tol : 1e-4) : (o->inner_tol > 0 ? o->inner_tol : o->tol);
   A.maxit = o->maxit;
-  A.max_outer = o->max_outer > 0 ? o->max_outer : (mixed ? 50 : 5);
+  A.max_outer = o->max_outer > 0 ? o->max_outer : (A.direct ? 100 : (mixed ? 50 : 5));
   A.ctl = c->ctl.as<DevCtl>();
   A.partial = c->partial.as<double>();
 
@@ -1974,10 +2032,12 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
 }
 
 // A QTT-preconditioned solve that breaks down (the rank-truncated inverse need
-// not be definite) is redone with the Jacobi preconditioner on the device.
+// not be definite), or a QTT direct solve whose refinement does not converge,
+// is redone with the Jacobi preconditioner on the device (stats.fallback = 1).
 static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_solve_opts* o) {
   qp_solve_stats st = solve_once(c, rhs, dx, o);
-  if (o->precond == QP_QTT_PCG && (st.status == QP_BREAKDOWN || st.status == QP_NOT_CONVERGED)) {
+  if ((o->precond == QP_QTT_PCG || o->precond == QP_QTT_DIRECT) &&
+      (st.status == QP_BREAKDOWN || st.status == QP_NOT_CONVERGED)) {
     qp_solve_opts j = *o;
     j.precond = QP_JACOBI_PCG;
     j.X = nullptr;
@@ -2131,6 +2191,35 @@ int pdip_step(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, qp_pdip_stats* st
   if (stats) *stats = out;
   return out.status;
   API_END(c)
+}
+
+int pdip_solve(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, double gap_tol, double dual_tol, int max_iter,
+               qp_pdip_stats* stats, int* iters) {
+  if (!c || !st || !o || max_iter < 0 || !(gap_tol >= 0.0) || !(dual_tol >= 0.0)) return QP_INVALID_ARG;
+  qp_pdip_stats last{};
+  int k = 0, rc = QP_OK;
+  for (;; ++k) {
+    double eta = 0.0, rd = 0.0;
+    rc = pdip_measure(c, st, &eta, &rd);
+    if (rc != QP_OK) break;
+    last.eta = eta;
+    last.r_dual = rd;
+    if (eta <= gap_tol && rd <= dual_tol) break;
+    if (k == max_iter) {
+      rc = QP_NOT_CONVERGED;
+      break;
+    }
+    rc = pdip_step(c, st, o, &last);
+    if (rc != QP_OK && rc != QP_NOT_CONVERGED) {
+      ++k;
+      break;
+    }
+    rc = QP_OK;
+  }
+  last.status = rc;
+  if (stats) *stats = last;
+  if (iters) *iters = k;
+  return rc;
 }
 
 }  // extern "C"

@@ -147,6 +147,38 @@ def test_failed_pipelined_solve_falls_back_on_fresh_context(ctx, mixed):
     assert np.linalg.norm(b - S @ pb.unpad(to_np(dx))) <= 1.05e-10 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("eps", [1e-12, 0.02, 0.1])
+def test_qtt_direct_mode_refines_to_tolerance(ctx, eps):
+    """QTT direct mode (Sec. 3.3): dx += X (rhs - S dx) with X the TT-SVD of the
+    exact inverse at eps.  On this 16-contact system an exact X needs one or two
+    steps; eps = 0.02 truncates the middle rank (spectral radius of I - S X
+    about 0.25, so many steps); eps = 0.1 makes it exceed 1 (1.27), the
+    refinement diverges and the solve falls back to Jacobi-PCG."""
+    from oracle import tt
+    pb = Problem(ctx, lattice_scene(2, 1))
+    g, lam = interior_point(pb, 4)
+    gd, ld, st = pb.state(g, lam)
+    rhs = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    pb.ctx.newton_rhs(st, rhs)
+    S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+    Sp = qp.padded_matrix(S, pb.Nc, 3, pb.P).toarray()
+    X = pb.ctx.qtt_from_cores(tt.qtt_inverse_dense(Sp, eps))
+    dx = torch.empty_like(rhs)
+    opts = pb.ctx.solve_opts(binding.QP_QTT_DIRECT, X, tol=1e-11, maxit=1000, max_outer=200)
+    stats = pb.ctx.newton_solve(st, rhs, dx, opts, allow=())
+    b = pb.unpad(to_np(rhs))
+    res = np.linalg.norm(b - S @ pb.unpad(to_np(dx))) / np.linalg.norm(b)
+    assert res <= 1.05e-11 and stats.rel_res <= 1e-11
+    if eps == 0.1:
+        assert stats.fallback == 1
+        return
+    assert stats.fallback == 0 and stats.iters == stats.outer
+    if eps < 1e-10:
+        assert stats.outer <= 2
+    else:
+        assert 5 <= stats.outer <= 40
+
+
 def test_solve_zero_rhs(pile8):
     g, lam = pile8.iters[0]
     gd, ld, st = pile8.state(g, lam)

@@ -98,3 +98,38 @@ def test_single_step_with_qtt_refresh_matches_oracle(ctx):
     g2, l2, _ = pdip.pdip_step(pb.N, pb.r, pb.scene.mu, g1, l1)
     pb.ctx.pdip_step(st, opts, allow=())
     assert relerr(pb.unpad(to_np(gd)), g2) <= 1e-7
+
+
+def test_pdip_solve_loop_matches_oracle(ctx):
+    """pdip_solve runs the loop of Sec. 2.4 to the tolerances: same iterate and
+    iteration count as the oracle's loop."""
+    s = lattice_scene(2, 1)
+    pb = Problem(ctx, s)
+    res = pdip.pdip_solve(pb.N, pb.r, s.mu, tol_gap=1e-8, tol_dual=1e-6, maxit=200)
+    assert res.converged
+    g0, l0 = qp.initial_point(pb.Nc, s.mu)
+    gd, ld, st = pb.state(g0, l0)
+    pb.ctx.pdip_init(st, 1.0)
+    stats, n = pb.ctx.pdip_solve(st, gpu_opts(pb.ctx), gap_tol=1e-8, dual_tol=1e-6, max_iter=200, allow=())
+    assert stats.status == binding.QP_OK
+    assert abs(n - res.iters) <= 1
+    assert stats.eta <= 1e-8 and stats.r_dual <= 1e-6
+    assert relerr(pb.unpad(to_np(gd)), res.gamma) <= 1e-6
+
+
+def test_pdip_solve_sphere_on_plane_and_cap(ctx):
+    s = sphere_on_plane((2.0, 0.5, -0.1))
+    pb = Problem(ctx, s)
+    want, k = closed_form(s.mass[0], s.mu, pb.r[0], pb.r[1:3])
+    g0, l0 = qp.initial_point(pb.Nc, s.mu)
+    gd, ld, st = pb.state(g0, l0)
+    pb.ctx.pdip_init(st, 1.0)
+    stats, n = pb.ctx.pdip_solve(st, gpu_opts(pb.ctx), gap_tol=1e-12, dual_tol=1e-9, max_iter=200, allow=())
+    assert 0 < n < 200
+    gg = pb.unpad(to_np(gd))
+    assert np.allclose(gg, want, rtol=0, atol=1e-6 * max(1.0, np.abs(want).max()) * s.mass[0])
+    # a cap below the iterations needed returns QP_NOT_CONVERGED after exactly that many steps
+    gd2, ld2, st2 = pb.state(g0, l0)
+    pb.ctx.pdip_init(st2, 1.0)
+    stats2, n2 = pb.ctx.pdip_solve(st2, gpu_opts(pb.ctx), gap_tol=1e-12, dual_tol=1e-9, max_iter=2)
+    assert stats2.status == binding.QP_NOT_CONVERGED and n2 == 2
