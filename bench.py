@@ -156,6 +156,12 @@ def job_throughput(local_units, local_ms, world):
 
 
 # ---------------------------------------------------------------------- our arm
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pcg<float, void>
+# launch of the 40^3 window, from an ncu capture of this kernel version (caches
+# flushed by ncu before the launch).  Reset to None when the kernel changes.
+KPCG_DRAM_BYTES_PER_LAUNCH = 191.34e6
+
+
 def solve_bytes(Nc, M, nrow, iters, outer):
     """Algorithmic bytes of one Newton solve: S-apply per contact/body plus the
     PCG vector passes, FP32 inner iterations and FP64 outer residuals."""
@@ -348,7 +354,9 @@ def run_ours(args):
         "max_rel_res": max(relres), "pcg_ms_per_solve": statistics.mean(pcg_ms),
         "qtt_refresh_ms_per_step": statistics.mean(refresh_ms) if qtt else None,
         "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "hbm", "achieved": ach, "peak": peak,
-                     "unit": "GB/s", "frac": ach / peak, "peak_source": src, "traffic": None},
+                     "unit": "GB/s", "frac": ach / peak, "peak_source": src,
+                     "traffic": KPCG_DRAM_BYTES_PER_LAUNCH if args.workload == "pile40p" else None,
+                     "traffic_unit": "bytes per launch (one Newton solve)"},
         "qtt_pcg": qtt_out,
         "e2e": {"value": args.window * 1e3 / e2e_ms_max * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
