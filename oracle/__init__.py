@@ -11,6 +11,7 @@ Modules
   pdip     : primal-dual interior point iteration               (Sec. 2.4)
   krylov   : Jacobi-preconditioned CG                           (Sec. 3.3, 4.2)
   tt       : TT-SVD, rounding, QTT tensorisation and mat-vec    (Sec. 3.1, 3.2)
+  timestep : velocity/position update, warm start of the PDIP   (Sec. 2.3, 3.3)
 
 Parity status per function is stated in each module header; functions with no
 independent pin say "parity unpinned" there.
