@@ -113,6 +113,40 @@ typedef struct {
 /* Initial point of Sec. 3.3: gn = gn0 (> 0), gt = 0, lambda_i = -1/f_i.      */
 int pdip_init(qp_ctx_t ctx, qp_state* st, double gn0);
 
+/* Warm start from the previous time step (Sec. 3.3: most contacts persist
+ * from one step to the next).  prev describes the previous step's contact set:
+ * its pairs (body_a, body_b, [Nc] each) and its final impulses gamma (padded,
+ * prev->slots rows per contact); all device arrays owned by the caller, who
+ * must copy them before the ccp_assemble that replaces the contact set.  Each
+ * contact of the current set whose pair (a, b) is in prev takes that impulse
+ * moved into its cone's interior: gamma_n = max(gamma_n, gn0), gamma_t scaled
+ * to |gamma_t| <= shrink * mu * gamma_n; a new contact takes (gn0, 0, 0);
+ * dummy rows 0; lambda_i = -1/f_i (centred at t = 1), t = 1.
+ * QP_INVALID_ARG unless gn0 > 0, 0 < shrink <= 1, prev->slots in {3, 4}.    */
+typedef struct {
+  int Nc;
+  int slots;
+  const int* body_a;
+  const int* body_b;
+  const double* gamma;
+} qp_prev_contacts;
+int pdip_init_warm(qp_ctx_t ctx, qp_state* st, const qp_prev_contacts* prev, double gn0, double shrink);
+
+/* The time step around the CCP (Sec. 2.3, Eqs. force_balance_disc and
+ * particle_evolution_disc), for the context's current contact set (built by
+ * the last ccp_assemble from this scene) and the impulses st->gamma (padded,
+ * momentum units):
+ *   v' = (v + dt g) + M^-1 D gamma,  omega' = omega + I^-1 (D gamma)_torque,
+ *   x' = x + dt v'   (semi-implicit Euler; spheres need no orientation).
+ * pos_out, vel_out, omega_out: [3*M] SoA device arrays, written on the
+ * context's stream; they may be the scene's own pos/vel/omega (each body is
+ * read and written by one thread).  The contact set is left as it is:
+ * ccp_assemble on the new positions builds the next step's.
+ * QP_INVALID_ARG if scene->M differs from the assembled body count.         */
+int ccp_advance(qp_ctx_t ctx, const qp_scene* scene, const qp_state* st, double* pos_out, double* vel_out,
+                double* omega_out);
+
+
 /* y = S x with S = N + blockdiag(H_c(gamma, lambda)) (Schur complement of Eq.
  * qp_Newton_system, Sec. 3.3) and identity dummy rows; st == NULL gives
  * y = N x.  N = D^T M^-1 D is applied in factored form (Eq. Ndef): body

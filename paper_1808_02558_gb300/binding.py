@@ -24,7 +24,8 @@ QP_CG, QP_BICGSTAB = 0, 1
 QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
-           "newton_apply", "newton_rhs", "newton_solve", "pdip_step", "pdip_measure", "pdip_solve", "qtt_from_host",
+           "newton_apply", "newton_rhs", "newton_solve", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
+           "ccp_advance", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
 
@@ -45,6 +46,11 @@ class Contacts(C.Structure):
 
 class State(C.Structure):
     _fields_ = [("gamma", C.c_void_p), ("lam", C.c_void_p), ("t", C.c_double)]
+
+
+class PrevContacts(C.Structure):
+    _fields_ = [("Nc", C.c_int), ("slots", C.c_int), ("body_a", C.c_void_p), ("body_b", C.c_void_p),
+                ("gamma", C.c_void_p)]
 
 
 class SolveOpts(C.Structure):
@@ -95,6 +101,8 @@ def load(path: str = LIB_PATH):
         "pdip_step": (i, [vp, C.POINTER(State), C.POINTER(PdipOpts), C.POINTER(PdipStats)]),
         "pdip_measure": (i, [vp, C.POINTER(State), C.POINTER(d), C.POINTER(d)]),
         "pdip_solve": (i, [vp, C.POINTER(State), C.POINTER(PdipOpts), d, d, i, C.POINTER(PdipStats), C.POINTER(i)]),
+        "pdip_init_warm": (i, [vp, C.POINTER(State), C.POINTER(PrevContacts), d, d]),
+        "ccp_advance": (i, [vp, C.POINTER(Scene), C.POINTER(State), vp, vp, vp]),
         "qtt_from_host": (i, [vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(vp)]),
         "qtt_free": (i, [vp, vp]),
         "qtt_get_dims": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
@@ -227,7 +235,22 @@ class Context:
         out = Contacts()
         self._check(self.lib.ccp_assemble(self.h, C.byref(sc), C.byref(out)), "ccp_assemble")
         self.contacts = out
+        self.scene = (sc, scene_dev)
         return out
+
+    def advance(self, st: State):
+        """One time step of the assembled scene with impulses st.gamma; updates the
+        scene's device tensors (pos, vel, omega) in place."""
+        sc, dev = self.scene
+        self._check(self.lib.ccp_advance(self.h, C.byref(sc), C.byref(st), _ptr(dev["pos"]), _ptr(dev["vel"]),
+                                         _ptr(dev["omega"])), "ccp_advance")
+
+    def pdip_init_warm(self, st: State, prev_a, prev_b, prev_gamma, prev_slots=3, gn0=1.0, shrink=0.9):
+        """Warm start from the previous step's pairs and impulses (device tensors
+        the caller copied before re-assembly)."""
+        pc = PrevContacts(int(prev_a.numel()), int(prev_slots), _ptr(prev_a), _ptr(prev_b), _ptr(prev_gamma))
+        self._check(self.lib.pdip_init_warm(self.h, C.byref(st), C.byref(pc), float(gn0), float(shrink)),
+                    "pdip_init_warm")
 
     # ------------------------------------------------------------- PDIP / Newton
     @staticmethod

@@ -17,7 +17,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqttpdip.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["ctx.cu", "assemble.cu", "newton.cu", "qtt.cu", "qtt_linalg.cu", "qtt_inverse.cu", "qtt_static.cu"]
+SOURCES = ["ctx.cu", "assemble.cu", "newton.cu", "timestep.cu", "qtt.cu", "qtt_linalg.cu", "qtt_inverse.cu",
+           "qtt_static.cu"]
 
 
 def nvcc() -> str:

@@ -299,7 +299,7 @@ constexpr int gather_nb() {
 // Incidences are taken in batches (4 in FP32, 2 in FP64): their codes first,
 // then all record and operand loads of the batch, so they are in flight together.
 template <class T, class X, int NB = gather_nb<T>()>
-__device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int b) {
+__device__ __forceinline__ void body_gather_vals(const SysView<T>& s, const X& x, int b, T (&v)[6]) {
   T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
   const int e = __ldg(s.bptr + b + 1);
   for (int k0 = __ldg(s.bptr + b); k0 < e; k0 += NB) {
@@ -309,7 +309,17 @@ __device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int
     gather_batch<NB>(s, x, code, F0, F1, F2, Q0, Q1, Q2);
   }
   const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
-  T v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
+  v[0] = im * F0;
+  v[1] = im * F1;
+  v[2] = im * F2;
+  v[3] = iI * Q0;
+  v[4] = iI * Q1;
+  v[5] = iI * Q2;
+}
+template <class T, class X, int NB = gather_nb<T>()>
+__device__ __forceinline__ void body_gather(const SysView<T>& s, const X& x, int b) {
+  T v[6];
+  body_gather_vals<T, X, NB>(s, x, b, v);
   store_w(s.w, b, v);
 }
 
@@ -593,12 +603,20 @@ __device__ bool qtt_precond(const PcgArgs& A, const T* r, T* z) {
     if (!grid_barrier(A.ctl, gridDim.x)) return false;
     in = tmp;
   }
-  __shared__ T gc[4 * 16 * 16];
-  for (int k = q.d; k >= 1; --k) {
-    T* out = (k == 1) ? z : static_cast<T*>(((q.d - k) & 1) ? A.qw1 : A.qw0);
-    qtt_step_grid<T, T, TC>(q, k, in, out, items, gc, 4 * 16 * 16);
+  // one grid-synchronised pass per two cores where the ranks allow (else one)
+  constexpr int GQ = 2 * 12 * 12;
+  __shared__ Quad<T> gq[GQ];
+  T* gc = reinterpret_cast<T*>(gq);  // single-core staging (4 * 16 * 16 values fit in GQ quads)
+  int pass = 0;
+  for (int k = q.d; k >= 1; ++pass) {
+    const int bound = qtt_fuse_bound<T>(q, k, GQ);
+    const int next = bound ? k - 2 : k - 1;
+    T* out = (next == 0) ? z : static_cast<T*>((pass & 1) ? A.qw1 : A.qw0);
+    if (bound) qtt_step2_grid<T, T, TC>(q, k, in, out, gq, bound);
+    else qtt_step_grid<T, T, TC>(q, k, in, out, items, gc, 4 * GQ);
     if (!grid_barrier(A.ctl, gridDim.x)) return false;
     in = out;
+    k = next;
   }
   if (A.qtt_scaled) {
     for (long long i = tid; i < A.nrow; i += gsz) z[i] *= sqrt(dinv[i]);
@@ -1717,6 +1735,34 @@ __global__ void k_pdip_init(int Nc, int slots, long long P, double mu, double gn
   }
 }
 
+// Time step (Sec. 2.3, Eqs. force_balance_disc, particle_evolution_disc):
+// v' = (v + dt g) + M^-1 D gamma, omega' = omega + I^-1 (D gamma)_torque,
+// x' = x + dt v'.  SoA [3][M] in and out; one thread per body reads its inputs
+// before it writes, so outputs may alias inputs.
+__global__ void k_advance(SysView<double> s, const double* __restrict__ gamma, const double* pos,
+                          const double* vel, const double* omega, double dt, double gx, double gy, double gz,
+                          double* pos_o, double* vel_o, double* om_o) {
+  const int M = s.M;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < M; b += gridDim.x * blockDim.x) {
+    double w[6];
+    body_gather_vals(s, plain<double>(gamma), b, w);
+    const double v0 = (vel[b] + dt * gx) + w[0];
+    const double v1 = (vel[M + b] + dt * gy) + w[1];
+    const double v2 = (vel[2 * M + b] + dt * gz) + w[2];
+    const double o0 = omega[b] + w[3], o1 = omega[M + b] + w[4], o2 = omega[2 * M + b] + w[5];
+    const double x0 = pos[b] + dt * v0, x1 = pos[M + b] + dt * v1, x2 = pos[2 * M + b] + dt * v2;
+    vel_o[b] = v0;
+    vel_o[M + b] = v1;
+    vel_o[2 * M + b] = v2;
+    om_o[b] = o0;
+    om_o[M + b] = o1;
+    om_o[2 * M + b] = o2;
+    pos_o[b] = x0;
+    pos_o[M + b] = x1;
+    pos_o[2 * M + b] = x2;
+  }
+}
+
 template <class K>
 int coop_grid(qp_ctx* c, K kernel) {
   int per_sm = 0;
@@ -2075,6 +2121,25 @@ int pdip_init(qp_ctx_t c, qp_state* st, double gn0) {
   k_pdip_init<<<c->num_sms * 4, 256, 0, c->stream>>>(c->Nc, c->slots, c->P, c->mu, gn0, st->gamma, st->lambda);
   QP_CUDA(cudaGetLastError());
   st->t = 1.0;
+  API_END(c)
+}
+
+int ccp_advance(qp_ctx_t c, const qp_scene* sc, const qp_state* st, double* pos_out, double* vel_out,
+                double* omega_out) {
+  API_BEGIN(c)
+  QP_REQUIRE(st, QP_INVALID_ARG, "ccp_advance: null state");
+  check_ready(c, st);
+  QP_REQUIRE(sc && sc->pos && sc->vel && sc->omega && pos_out && vel_out && omega_out, QP_INVALID_ARG,
+             "ccp_advance: null scene array");
+  QP_REQUIRE(sc->M == c->M, QP_INVALID_ARG, "ccp_advance: scene is not the one of the current contact set");
+  if (c->M > 0) {
+    SysView<double> s = view64(c, false);
+    int grid = (c->M + 255) / 256;
+    if (grid > c->num_sms * 8) grid = c->num_sms * 8;
+    k_advance<<<grid, 256, 0, c->stream>>>(s, st->gamma, sc->pos, sc->vel, sc->omega, sc->dt, sc->gravity[0],
+                                           sc->gravity[1], sc->gravity[2], pos_out, vel_out, omega_out);
+    QP_CUDA(cudaGetLastError());
+  }
   API_END(c)
 }
 

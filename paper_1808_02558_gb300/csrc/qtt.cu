@@ -16,6 +16,32 @@ __global__ void k_qtt_step(QttDev q, int k, const TV* in, TV* out, long long ite
   qtt_step_grid<TV, TA, TC>(q, k, in, out, items, gc, QTT_GCAP);
 }
 
+constexpr int QTT_GQ = 2 * 12 * 12;  // staged quads of a fused pass (ranks up to 12)
+
+// Two blocks of 256 threads per SM (128 registers): the fused pass is limited by
+// FP32 issue and latency at rank 10, and the second block hides more of it.
+template <class TV, class TA, class TC>
+__global__ void __launch_bounds__(256, 2) k_qtt_step2(QttDev q, int k, const TV* in, TV* out, int bound) {
+  __shared__ Quad<TA> gq[QTT_GQ];
+  qtt_step2_grid<TV, TA, TC>(q, k, in, out, gq, bound);
+}
+
+template <class TV, class TA, class TC>
+void launch_step(qp_ctx* c, const QttDev& q, int k, const void* in, void* out, int bound, long long N) {
+  const TV* i = static_cast<const TV*>(in);
+  TV* o = static_cast<TV*>(out);
+  if (bound) {
+    long long want = ((N >> 2) + 255) / 256;
+    if (want > (long long)c->num_sms * 16) want = (long long)c->num_sms * 16;
+    k_qtt_step2<TV, TA, TC><<<(int)(want < 1 ? 1 : want), 256, 0, c->stream>>>(q, k, i, o, bound);
+  } else {
+    const long long items = N >> 1;
+    long long want = (items + 511) / 512;  // two columns per thread
+    if (want > (long long)c->num_sms * 16) want = (long long)c->num_sms * 16;
+    k_qtt_step<TV, TA, TC><<<(int)(want < 1 ? 1 : want), 256, 0, c->stream>>>(q, k, i, o, items);
+  }
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -90,7 +116,8 @@ static QttDev dev_view(qp_qtt* A, const void* cores) {
   return q;
 }
 
-// y = A x: d launches of the column step, ping-ponging between two work buffers.
+// y = A x: one launch per pass (two cores per pass where the ranks allow, else
+// one), ping-ponging between two work buffers.
 void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype cdt, qp_dtype vdt) {
   QP_REQUIRE(vdt == QP_F64 || vdt == QP_F32, QP_INVALID_ARG, "qtt_apply: vector dtype must be F64 or F32");
   QP_REQUIRE(!(vdt == QP_F64 && cdt != QP_F64), QP_INVALID_ARG, "qtt_apply: F64 vectors need F64 cores");
@@ -103,29 +130,19 @@ void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype cdt
   const size_t es = vdt == QP_F64 ? sizeof(double) : sizeof(float);
   void* w0 = c->scratch[5].ensure((size_t)N * q.rmax * es);
   void* w1 = c->scratch[6].ensure((size_t)N * q.rmax * es);
-  const long long items = N >> 1;
-  // two columns per thread
-  long long want = (items + 511) / 512;
-  if (want > (long long)c->num_sms * 16) want = (long long)c->num_sms * 16;
-  const int grid = (int)(want < 1 ? 1 : want);
   const void* in = x;
-  for (int k = A->d; k >= 1; --k) {
-    void* out = (k == 1) ? y : (((A->d - k) & 1) ? w1 : w0);
-    if (vdt == QP_F64) {
-      k_qtt_step<double, double, double><<<grid, 256, 0, c->stream>>>(q, k, static_cast<const double*>(in),
-                                                                       static_cast<double*>(out), items);
-    } else if (cdt == QP_F32) {
-      k_qtt_step<float, float, float><<<grid, 256, 0, c->stream>>>(q, k, static_cast<const float*>(in),
-                                                                   static_cast<float*>(out), items);
-    } else if (cdt == QP_BF16) {
-      k_qtt_step<float, float, __nv_bfloat16><<<grid, 256, 0, c->stream>>>(q, k, static_cast<const float*>(in),
-                                                                           static_cast<float*>(out), items);
-    } else {
-      k_qtt_step<float, float, double><<<grid, 256, 0, c->stream>>>(q, k, static_cast<const float*>(in),
-                                                                    static_cast<float*>(out), items);
-    }
+  int pass = 0;
+  for (int k = A->d; k >= 1; ++pass) {
+    const int bound = vdt == QP_F64 ? 0 : qtt_fuse_bound<float>(q, k, QTT_GQ);
+    const int next = bound ? k - 2 : k - 1;
+    void* out = (next == 0) ? y : ((pass & 1) ? w1 : w0);
+    if (vdt == QP_F64) launch_step<double, double, double>(c, q, k, in, out, bound, N);
+    else if (cdt == QP_F32) launch_step<float, float, float>(c, q, k, in, out, bound, N);
+    else if (cdt == QP_BF16) launch_step<float, float, __nv_bfloat16>(c, q, k, in, out, bound, N);
+    else launch_step<float, float, double>(c, q, k, in, out, bound, N);
     QP_CUDA(cudaGetLastError());
     in = out;
+    k = next;
   }
 }
 

@@ -193,6 +193,159 @@ __device__ __forceinline__ void qtt_step_block(const QttDev& q, int k, const TV*
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- two cores per pass
+// Steps k and k-1 fused: a column (J'', I), J'' = (j_1..j_{k-2}), I =
+// (i_{k+1}..i_d), reads the 4 r_k inputs Z_{k+1}[4J''+2j_{k-1}+j_k][b][I],
+// forms the 4 r_{k-1} values of Z_k in registers and writes the 4 r_{k-2}
+// outputs Z_{k-1}[J''][c][(2 i_{k-1} + i_k) 2^(d-k) + I].  Each pass moves
+// (r_k + r_{k-2}) N values instead of (r_k + 2 r_{k-1} + r_{k-2}) N.
+// Both cores are staged in shared memory as one 4-vector (i, j) per rank pair:
+// gk[a r_k + b] = G_k(a, ., ., b), gm[c r_{k-1} + a] = G_{k-1}(c, ., ., a).
+template <class TA>
+struct Quad {
+  TA v[4];
+};
+template <>
+struct Quad<float> {
+  float4 q;
+};
+template <class TA>
+__device__ __forceinline__ void quad_get(const Quad<TA>& g, TA& g00, TA& g01, TA& g10, TA& g11) {
+  g00 = g.v[0]; g01 = g.v[1]; g10 = g.v[2]; g11 = g.v[3];
+}
+__device__ __forceinline__ void quad_get(const Quad<float>& g, float& g00, float& g01, float& g10, float& g11) {
+  const float4 q = g.q;
+  g00 = q.x; g01 = q.y; g10 = q.z; g11 = q.w;
+}
+template <class TA>
+__device__ __forceinline__ void quad_set(Quad<TA>& g, TA g00, TA g01, TA g10, TA g11) {
+  g.v[0] = g00; g.v[1] = g01; g.v[2] = g10; g.v[3] = g11;
+}
+__device__ __forceinline__ void quad_set(Quad<float>& g, float g00, float g01, float g10, float g11) {
+  g.q = make_float4(g00, g01, g10, g11);
+}
+
+template <class TA, class TC>
+__device__ __forceinline__ TA core_ta(const TC* G, long long i) {
+  if constexpr (sizeof(TC) == 8) return (TA)G[i];
+  else return (TA)core_f<TC>(G, i);
+}
+
+// Stage core kk (1-based) as quads: out[a * rin + b] = G_kk(a, ., ., b).
+template <class TA, class TC>
+__device__ __forceinline__ void stage_quads(const QttDev& q, int kk, Quad<TA>* out) {
+  const int ro = q.ranks[kk - 1], ri = q.ranks[kk];
+  const TC* G = static_cast<const TC*>(q.cores) + q.off[kk - 1];
+  for (int t = threadIdx.x; t < ro * ri; t += blockDim.x) {
+    const int a = t / ri, b = t - a * ri;
+    const long long base = (long long)a * 4 * ri + b;
+    quad_set(out[t], core_ta<TA, TC>(G, base), core_ta<TA, TC>(G, base + ri), core_ta<TA, TC>(G, base + 2 * ri),
+             core_ta<TA, TC>(G, base + 3 * ri));
+  }
+}
+
+// Requires r_k, r_{k-1} <= R and r_{k-1} r_k + r_{k-2} r_{k-1} <= gcap quads.
+// All threads of the block call it (it synchronises).
+template <int R, class TV, class TA, class TC>
+__device__ __forceinline__ void qtt_step2_block(const QttDev& q, int k, const TV* in, TV* out, Quad<TA>* gq,
+                                                long long first, long long stride) {
+  const int d = q.d;
+  const int r2 = q.ranks[k - 2], r0 = q.ranks[k - 1], r1 = q.ranks[k];
+  Quad<TA>* gk = gq;
+  Quad<TA>* gm = gq + r0 * r1;
+  stage_quads<TA, TC>(q, k, gk);
+  stage_quads<TA, TC>(q, k - 1, gm);
+  __syncthreads();
+  const int lowbits = d - k;
+  const long long nI = 1LL << lowbits;
+  const long long cols = 1LL << (d - 2);
+  for (long long it = first; it < cols; it += stride) {
+    const long long I = it & (nI - 1), J = it >> lowbits;
+    // inputs v[2 j_{k-1} + j_k][b]
+    TA v[4][R];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const TV* src = in + ((4 * J + jj) * r1) * nI + I;
+#pragma unroll
+      for (int b = 0; b < R; ++b) v[jj][b] = b < r1 ? (TA)src[(long long)b * nI] : TA(0);
+    }
+    // step k: t[j_{k-1}][i_k][a]
+    TA t[2][2][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      TA s00 = 0, s01 = 0, s10 = 0, s11 = 0;  // [j_{k-1}][i_k]
+      if (a < r0) {
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          if (b < r1) {
+            TA g00, g01, g10, g11;  // G_k(a, i, j, b)
+            quad_get(gk[a * r1 + b], g00, g01, g10, g11);
+            s00 += g00 * v[0][b] + g01 * v[1][b];
+            s01 += g10 * v[0][b] + g11 * v[1][b];
+            s10 += g00 * v[2][b] + g01 * v[3][b];
+            s11 += g10 * v[2][b] + g11 * v[3][b];
+          }
+        }
+      }
+      t[0][0][a] = s00;
+      t[0][1][a] = s01;
+      t[1][0][a] = s10;
+      t[1][1][a] = s11;
+    }
+    // step k-1: outputs [c][2 i_{k-1} + i_k]
+    TV* o = out + (J * r2) * (4 * nI) + I;
+    for (int c = 0; c < r2; ++c) {
+      TA y00 = 0, y01 = 0, y10 = 0, y11 = 0;  // [i_{k-1}][i_k]
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        if (a < r0) {
+          TA g00, g01, g10, g11;  // G_{k-1}(c, i, j, a)
+          quad_get(gm[c * r0 + a], g00, g01, g10, g11);
+          y00 += g00 * t[0][0][a] + g01 * t[1][0][a];
+          y01 += g00 * t[0][1][a] + g01 * t[1][1][a];
+          y10 += g10 * t[0][0][a] + g11 * t[1][0][a];
+          y11 += g10 * t[0][1][a] + g11 * t[1][1][a];
+        }
+      }
+      TV* oc = o + (long long)c * 4 * nI;
+      oc[0] = (TV)y00;
+      oc[nI] = (TV)y01;
+      oc[2 * nI] = (TV)y10;
+      oc[3 * nI] = (TV)y11;
+    }
+  }
+  __syncthreads();
+}
+
+// Rank bound of the fused pass for cores k, k-1 (0: not fusable).  Only FP32
+// accumulation is fused: FP64 intermediates of rank 12 do not fit the registers.
+template <class TA>
+__host__ __device__ __forceinline__ int qtt_fuse_bound(const QttDev& q, int k, int gcap_quads) {
+  if (sizeof(TA) != 4 || k < 2) return 0;
+  const int r2 = q.ranks[k - 2], r0 = q.ranks[k - 1], r1 = q.ranks[k];
+  if (r0 * r1 + r2 * r0 > gcap_quads) return 0;
+  const int r = r0 > r1 ? r0 : r1;
+  if (r <= 4) return 4;
+  if (r <= 8) return 8;
+  if (r <= 10) return 10;  // the paper's operating rank
+  if (r <= 12) return 12;
+  return 0;
+}
+
+// Grid-stride fused pass with the block dispatch on the rank bound.
+template <class TV, class TA, class TC>
+__device__ __forceinline__ void qtt_step2_grid(const QttDev& q, int k, const TV* in, TV* out, Quad<TA>* gq,
+                                               int bound) {
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (sizeof(TA) == 4) {
+    if (bound == 4) qtt_step2_block<4, TV, TA, TC>(q, k, in, out, gq, first, stride);
+    else if (bound == 8) qtt_step2_block<8, TV, TA, TC>(q, k, in, out, gq, first, stride);
+    else if (bound == 10) qtt_step2_block<10, TV, TA, TC>(q, k, in, out, gq, first, stride);
+    else qtt_step2_block<12, TV, TA, TC>(q, k, in, out, gq, first, stride);
+  }
+}
+
 // Block-level dispatch on the input rank; falls back to the per-item step
 // (cores read from global memory) for ranks above 32 or cores larger than gcap.
 template <class TV, class TA, class TC>

@@ -24,7 +24,9 @@ def random_cores(d, rmax, seed):
     return [rng.standard_normal((r[k], 4, r[k + 1])) / np.sqrt(2 * r[k + 1]) for k in range(d)]
 
 
-@pytest.mark.parametrize("d,rmax", [(1, 1), (2, 3), (10, 8), (13, 17)])
+# ranks <= 12 take the two-cores-per-pass kernel in FP32/BF16, larger ranks (and
+# FP64) the one-core kernel; (13, 17) and (15, 14) mix both within one apply
+@pytest.mark.parametrize("d,rmax", [(1, 1), (2, 3), (3, 12), (10, 8), (13, 17), (15, 14)])
 def test_apply_random_cores(ctx, d, rmax):
     cores = random_cores(d, rmax, d)
     A = ctx.qtt_from_cores(cores)
@@ -68,6 +70,10 @@ def test_apply_full_size_d20(ctx):
     y = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
     ctx.qtt_apply(A, dev(x), y)
     assert relerr(to_np(y), want) <= 1e-13
+    x32 = dev(x).float()
+    y32 = torch.empty_like(x32)
+    ctx.qtt_apply(A, x32, y32, binding.QP_F32, binding.QP_F32)
+    assert relerr(to_np(y32).astype(np.float64), want) <= 2e-4
 
 
 # ---------------------------------------------------------------- rounding (Sec. 3.1)
