@@ -369,6 +369,9 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_ms_max = max_over_ranks(statistics.median(e2e_ms), world)
 
+    ts_out = time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream) if args.ts_steps > 0 else None
+    batch_out = batched_leg(args, binding, workload) if args.batch_scenes > 0 else None
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -391,6 +394,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "time_stepping": ts_out,
+        "batched": batch_out,
     }
     if rank == 0 and not args.no_cpu_baseline:
         ctx.pdip_init(st, 1.0)
@@ -403,6 +408,126 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def batched_leg(args, binding, workload):
+    """Many small scenes (sides U{4..16}, mu U[0.2, 0.8], seeded): the Newton system
+    at the cold start of each, solved to 1e-8 by one launch over the scene table
+    (one thread block per scene) and, for comparison, by one newton_solve per scene."""
+    import torch
+
+    from synth import lattice_scene, splitmix64_uniform
+
+    n = args.batch_scenes
+    u = splitmix64_uniform(7, 31, 2 * n)
+    sides = [4 + min(12, int(x * 13)) for x in u[:n]]
+    mus = [0.2 + 0.6 * x for x in u[n:]]
+    ctxs, states, rhs, dx, keep = [], [], [], [], []
+    nc_tot, p_tot = 0, 0
+    for i in range(n):
+        sc = lattice_scene(sides[i], 100 + i, mu=mus[i])
+        c = binding.Context()
+        _, con = workload.assemble(c, sc)
+        g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+        st = c.state(g, lam)
+        c.pdip_init(st, 1.0)
+        r = torch.empty(con.P, dtype=torch.float64, device="cuda")
+        c.newton_rhs(st, r)
+        ctxs.append(c)
+        states.append(st)
+        rhs.append(r)
+        dx.append(torch.empty_like(r))
+        keep.append((g, lam))
+        nc_tot += con.Nc
+        p_tot += con.P
+    torch.cuda.synchronize()
+    kw = dict(tol=1e-8, maxit=100000, inner_tol=1e-3, max_outer=60)
+    stats, used = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=0, **kw)  # measures the block size
+    t_b = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats, used = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=used, **kw)
+        t_b.append(time.perf_counter() - t0)
+    so = [c.solve_opts(tol=1e-8, maxit=100000, mixed=1, inner_tol=1e-3, max_outer=60) for c in ctxs]
+    one = [torch.empty_like(r) for r in rhs]
+    for c, st, r, x, o in zip(ctxs, states, rhs, one, so):  # warm-up pass
+        c.newton_solve(st, r, x, o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, st, r, x, o in zip(ctxs, states, rhs, one, so):
+        c.newton_solve(st, r, x, o)
+    torch.cuda.synchronize()
+    t_s = time.perf_counter() - t0
+    tb = statistics.median(t_b)
+    out = {"scenes": n, "sides": "U{4..16}", "mu": "U[0.2, 0.8]", "contacts": nc_tot, "padded_unknowns": p_tot,
+           "block_threads": used, "tol": 1e-8, "batched_ms": tb * 1e3, "batched_device_ms": stats[0].ms,
+           "batched_solves_per_s": n / tb, "sequential_ms": t_s * 1e3, "sequential_solves_per_s": n / t_s,
+           "speedup": t_s / tb, "max_rel_res": max(s.rel_res for s in stats),
+           "not_converged": sum(1 for s in stats if s.status != binding.QP_OK),
+           "iters_mean": statistics.mean(s.iters for s in stats)}
+    for c in ctxs:
+        c.close()
+    return out
+
+
+def time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream):
+    """Time steps of the scene (Sec. 2.3): assemble, PDIP init (cold at the first
+    step, warm from the persisting contacts after), a window of PDIP iterations,
+    advance.  Reports the time per step and its parts, the fraction of contacts
+    that persist, and, at every warm-started step, the surrogate gap and dual
+    residual after the window against a cold start of the same system."""
+    import torch
+
+    ctx = binding.Context()
+    dev_s = workload.scene_to_device(scene, "cuda")
+    rows, prev = [], None
+    for step in range(args.ts_steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        con = ctx.assemble(dev_s, scene.floor_z, scene.gravity, scene.dt, scene.delta, scene.mu, 3)
+        ev[1].record(stream)
+        g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+        st = ctx.state(g, lam)
+        if prev is None:
+            ctx.pdip_init(st, 1.0)
+        else:
+            ctx.pdip_init_warm(st, prev[0], prev[1], prev[2], 3)
+        for _ in range(args.window):
+            ctx.pdip_step(st, opts, allow=ok)
+        ev[2].record(stream)
+        ab = (workload.view(con, "body_a"), workload.view(con, "body_b"))
+        eta, rd = ctx.pdip_measure(st)
+        cold = None
+        if prev is not None:
+            # the same system from the cold start, for comparison (not timed)
+            g2 = torch.zeros_like(g)
+            l2 = torch.zeros_like(lam)
+            st2 = ctx.state(g2, l2)
+            ctx.pdip_init(st2, 1.0)
+            for _ in range(args.window):
+                ctx.pdip_step(st2, opts, allow=ok)
+            cold = ctx.pdip_measure(st2)
+        ev3 = torch.cuda.Event(enable_timing=True)
+        ev3.record(stream)
+        ctx.advance(st)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        keys = set(zip(ab[0].tolist(), ab[1].tolist()))
+        persist = None if prev is None else len(keys & prev[3]) / max(1, len(keys))
+        rows.append({"step": step, "contacts": con.Nc, "persisting": persist,
+                     "ms_assemble": ev[0].elapsed_time(ev[1]), "ms_pdip_window": ev[1].elapsed_time(ev[2]),
+                     "ms_advance": ev3.elapsed_time(ev[3]), "eta": eta, "r_dual": rd,
+                     "cold_eta": None if cold is None else cold[0], "cold_r_dual": None if cold is None else cold[1]})
+        prev = (ab[0], ab[1], g.clone(), keys)
+    ctx.close()
+    ms = [r["ms_assemble"] + r["ms_pdip_window"] + r["ms_advance"] for r in rows]
+    return {"steps": args.ts_steps, "pdip_iterations_per_step": args.window,
+            "ms_per_time_step": sum(ms) / len(ms), "per_step": rows,
+            "note": "Jacobi-PCG windows; warm start = previous impulses of persisting pairs moved into the cone"}
 
 
 # ---------------------------------------------------------------------- oracle arm
@@ -502,6 +627,8 @@ def main():
     ap.add_argument("--qtt-eps", type=float, default=1e-2)
     ap.add_argument("--qtt-rmax", type=int, default=10)
     ap.add_argument("--qtt-steps", type=int, default=1, help="PDIP steps of the QTT-PCG comparison leg (0: skip)")
+    ap.add_argument("--ts-steps", type=int, default=3, help="time steps of the time-stepping leg (0: skip)")
+    ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
     ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],
                     help="Krylov method of the QTT leg (the paper uses BiCGSTAB)")
     ap.add_argument("--qtt-maxit", type=int, default=2000,

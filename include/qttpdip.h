@@ -197,6 +197,29 @@ typedef struct {
 int newton_solve(qp_ctx_t ctx, const qp_state* st, const double* rhs, double* dx,
                  const qp_solve_opts* opts, qp_solve_stats* stats);
 
+/* Batched Newton solves (many independent scenes in one launch): scene i is
+ * the current contact set of ctxs[i] with state st[i] (NULL: S = N), solved
+ * for rhs[i] -> dx[i] (device, P_i doubles each, not aliased).  One thread
+ * block per scene builds the Schur blocks and the Jacobi diagonal and runs
+ * FP32 Jacobi-PCG to inner_tol inside FP64 iterative refinement to tol, with
+ * block-level synchronisation only; scenes start in decreasing size.  All
+ * contexts must be on one device; the launch goes to ctxs[0]'s stream after
+ * the other contexts' streams, and their later work waits for it.
+ * block_threads: 128, 256, 512 or 1024, or 0 to pick the fastest of 256, 512
+ * and 1024 by timing this batch (the choice is kept per device and batch
+ * size class).  stats[i] (may be NULL): per-scene statistics; *used (may be
+ * NULL): the block size used.  Returns QP_OK when every scene converged, else
+ * QP_NOT_CONVERGED or QP_BREAKDOWN (first failing scene in stats).          */
+typedef struct {
+  double tol;          /* FP64 relative residual target                      */
+  int maxit;           /* inner iteration cap per scene                      */
+  double inner_tol;    /* FP32 inner relative tolerance (0: 1e-3)            */
+  int max_outer;       /* refinement cap (0: 50)                             */
+  int block_threads;   /* see above                                          */
+} qp_batch_opts;
+int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st, const double* const* rhs,
+                         double* const* dx, const qp_batch_opts* opts, qp_solve_stats* stats, int* used);
+
 typedef struct {
   double nu;          /* t = nu * 2Nc / eta                         (10)       */
   double alpha;       /* sufficient-decrease factor                 (0.01)     */

@@ -24,7 +24,7 @@ QP_CG, QP_BICGSTAB = 0, 1
 QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
-           "newton_apply", "newton_rhs", "newton_solve", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
+           "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
            "ccp_advance", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
@@ -46,6 +46,11 @@ class Contacts(C.Structure):
 
 class State(C.Structure):
     _fields_ = [("gamma", C.c_void_p), ("lam", C.c_void_p), ("t", C.c_double)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
+                ("block_threads", C.c_int)]
 
 
 class PrevContacts(C.Structure):
@@ -102,6 +107,8 @@ def load(path: str = LIB_PATH):
         "pdip_measure": (i, [vp, C.POINTER(State), C.POINTER(d), C.POINTER(d)]),
         "pdip_solve": (i, [vp, C.POINTER(State), C.POINTER(PdipOpts), d, d, i, C.POINTER(PdipStats), C.POINTER(i)]),
         "pdip_init_warm": (i, [vp, C.POINTER(State), C.POINTER(PrevContacts), d, d]),
+        "newton_solve_batched": (i, [i, C.POINTER(vp), C.POINTER(C.POINTER(State)), C.POINTER(vp), C.POINTER(vp),
+                                     C.POINTER(BatchOpts), C.POINTER(SolveStats), C.POINTER(i)]),
         "ccp_advance": (i, [vp, C.POINTER(Scene), C.POINTER(State), vp, vp, vp]),
         "qtt_from_host": (i, [vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(vp)]),
         "qtt_free": (i, [vp, vp]),
@@ -334,3 +341,23 @@ class Context:
         self._check(self.lib.qtt_inverse(self.h, S.h, float(eps), int(rmax), int(sweeps),
                                          warm.h if warm is not None else None, C.byref(h)), "qtt_inverse")
         return QTT(self, h.value)
+
+
+def newton_solve_batched(ctxs, states, rhs, dx, tol=1e-8, maxit=100000, inner_tol=1e-3, max_outer=60,
+                         block_threads=0, allow=(QP_NOT_CONVERGED, QP_BREAKDOWN)):
+    """Many scenes in one launch (one thread block per scene).  ctxs: Contexts on
+    one device; states: State or None per scene; rhs, dx: device tensors.
+    Returns (per-scene SolveStats list, block size used)."""
+    lib = load()
+    n = len(ctxs)
+    ch = (C.c_void_p * n)(*[c.h.value for c in ctxs])
+    sp = (C.POINTER(State) * n)(*[C.pointer(s) if s is not None else C.POINTER(State)() for s in states])
+    rp = (C.c_void_p * n)(*[_ptr(t) for t in rhs])
+    dp = (C.c_void_p * n)(*[_ptr(t) for t in dx])
+    opts = BatchOpts(float(tol), int(maxit), float(inner_tol), int(max_outer), int(block_threads))
+    stats = (SolveStats * n)()
+    used = C.c_int(0)
+    rc = lib.newton_solve_batched(n, ch, sp, rp, dp, C.byref(opts), stats, C.byref(used))
+    if rc != QP_OK and rc not in allow:
+        ctxs[0]._check(rc, "newton_solve_batched")
+    return list(stats), used.value

@@ -102,7 +102,8 @@ struct qp_ctx {
   // contact partition of the fused Krylov kernel (one contiguous chunk per block)
   int part_G = 0, part_chunk = 0, part_maxb = 0, part_nbmax = 0;
   qp::Buf part_nb, part_bodies, part_cl;
-  qp::Buf fused_pool;  // records of the fused pipelined solver (never shared with the classic solver)
+  qp::Buf fused_pool;
+  qp::Buf batch64, batch32, batch_table;  // batched solves: per-scene vectors; table (first context)  // records of the fused pipelined solver (never shared with the classic solver)
 };
 
 namespace qp {

@@ -16,6 +16,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <vector>
 
@@ -546,6 +548,24 @@ __global__ void k_schur_blocks(PdipView v, double* __restrict__ H, float* __rest
   }
 }
 
+// Diagonal entry (c, u) of N = D^T M^-1 D: sum over the contact's dynamic
+// bodies of 1/m + (rho x U_u)^T I^-1 (rho x U_u).
+__device__ __forceinline__ double diag_entry(const SysView<double>& s, int c, int u) {
+  double R[16];
+  load_rec(s.rec, c, R);
+  const double U0 = R[3 * u], U1 = R[3 * u + 1], U2 = R[3 * u + 2];
+  const int a = s.ca[c], b = s.cb[c];
+  double t0 = R[13] * U2 - R[14] * U1, t1 = R[14] * U0 - R[12] * U2, t2 = R[12] * U1 - R[13] * U0;
+  double v = s.inv_m[b] + s.inv_I[b] * (t0 * t0 + t1 * t1 + t2 * t2);
+  if (a < s.M) {
+    t0 = R[10] * U2 - R[11] * U1;
+    t1 = R[11] * U0 - R[9] * U2;
+    t2 = R[9] * U1 - R[10] * U0;
+    v += s.inv_m[a] + s.inv_I[a] * (t0 * t0 + t1 * t1 + t2 * t2);
+  }
+  return v;
+}
+
 // ------------------------------------------------------------------ PCG kernel
 struct PcgArgs {
   SysView<double> s64;
@@ -1036,6 +1056,207 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
   }
 }
 
+// ------------------------------------------------------------------ batched scenes
+// Many independent Newton solves in one launch: one thread block per scene runs
+// the whole solve (Schur blocks, Jacobi diagonal, FP32 inner PCG, FP64
+// refinement) with block-level synchronisation only.  Scenes are taken in
+// decreasing size, so the largest start first.
+struct BatchScene {
+  SysView<double> s64;   // H = the scene's FP64 block buffer (written here)
+  SysView<float> s32;
+  double* H64;
+  float* H32;
+  double* dinv64;
+  float* dinv32;
+  const double* gamma;   // null: S = N
+  const double* lambda;
+  double mu;
+  const double* rhs;
+  double* dx;
+  double* r64;           // [P] FP64 residual
+  double* q64;           // [P]
+  float* v32;            // 7 [P] FP32 vectors: b, e, r, z, p, p', q
+  long long P;
+  int nrow;
+};
+
+struct BatchOut {
+  int iters, outer, status, pad;
+  double rel;
+};
+
+template <int NTB, class V, int K>
+__device__ __forceinline__ void block_sum(V (&v)[K]) {
+  __shared__ V sm[K][NTB / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < K; ++k) {
+    const V x = warp_sum(v[k]);
+    if (lane == 0) sm[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    for (int k = 0; k < K; ++k) {
+      V x = lane < NTB / 32 ? sm[k][lane] : V(0);
+      x = warp_sum(x);
+      if (lane == 0) sm[k][0] = x;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < K; ++k) v[k] = sm[k][0];
+  __syncthreads();
+}
+
+// FP32 inner PCG of one scene on S e = b (block-local).  Returns 0 converged,
+// 1 cap, 2 breakdown.
+template <int NTB>
+__device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& iters) {
+  const SysView<float>& s = S.s32;
+  const int nrow = S.nrow, t = threadIdx.x;
+  const long long P = S.P;
+  float* b = S.v32;
+  float* e = b + P;
+  float* r = e + P;
+  float* z = r + P;
+  float* pa = z + P;
+  float* pb = pa + P;
+  float* q = pb + P;
+  const float* dinv = S.dinv32;
+  float a0[2] = {0.f, 0.f};
+  for (int i = t; i < nrow; i += NTB) {
+    const float bi = b[i];
+    e[i] = 0.f;
+    r[i] = bi;
+    const float zi = dinv[i] * bi;
+    z[i] = zi;
+    a0[0] += bi * bi;
+    a0[1] += bi * zi;
+  }
+  block_sum<NTB>(a0);
+  const float bb = a0[0];
+  float rz = a0[1];
+  if (bb == 0.f) return 0;
+  const float stop = tol * tol * bb;
+  float* pold = pa;
+  float* pnew = pb;
+  float beta = 0.f;
+  for (int it = 0; it < maxit; ++it) {
+    if (!(rz > 0.f)) return 2;
+    const Operand<float> dir{z, it == 0 ? nullptr : pold, beta};
+    for (int bd = t; bd < s.M; bd += NTB) body_gather(s, dir, bd);
+    __syncthreads();
+    float a1[1] = {0.f};
+    for (int c = t; c < s.Nc; c += NTB) a1[0] += contact_apply(s, dir, q, c, pnew);
+    block_sum<NTB>(a1);
+    const float pq = a1[0];
+    if (!(pq > 0.f)) return 2;
+    const float alpha = rz / pq;
+    float a2[2] = {0.f, 0.f};
+    for (int i = t; i < nrow; i += NTB) {
+      e[i] += alpha * pnew[i];
+      const float ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      const float zi = dinv[i] * ri;
+      z[i] = zi;
+      a2[0] += ri * ri;
+      a2[1] += ri * zi;
+    }
+    block_sum<NTB>(a2);
+    ++iters;
+    if (a2[0] <= stop) return 0;
+    beta = a2[1] / rz;
+    rz = a2[1];
+    float* tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+  }
+  return 1;
+}
+
+template <int NTB>
+__global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restrict__ tab, const int* __restrict__ order,
+                                                     double tol, double inner_tol, int maxit, int max_outer,
+                                                     BatchOut* __restrict__ out) {
+  const int sid = order[blockIdx.x];
+  const BatchScene S = tab[sid];
+  const int t = threadIdx.x;
+  const int n = S.s64.Nc;
+  // Schur blocks (zero without a state) and the Jacobi diagonal
+  for (int c = t; c < n; c += NTB) {
+    double h[6] = {0, 0, 0, 0, 0, 0};
+    if (S.gamma) {
+      const long long row = (long long)S.s64.slots * c;
+      schur_block(S.mu, S.gamma[row], S.gamma[row + 1], S.gamma[row + 2], S.lambda[c], S.lambda[n + c], h);
+    }
+    for (int k = 0; k < 6; ++k) {
+      S.H64[(size_t)k * n + c] = h[k];
+      S.H32[(size_t)k * n + c] = (float)h[k];
+    }
+  }
+  __syncthreads();
+  for (long long i = t; i < S.P; i += NTB) {
+    const long long c = i / S.s64.slots;
+    const int u = (int)(i - c * S.s64.slots);
+    double v = 1.0;
+    if (c < n && u < 3) v = diag_entry(S.s64, (int)c, u) + S.H64[(u == 0 ? 0 : (u == 1 ? 3 : 5)) * (long long)n + c];
+    S.dinv64[i] = 1.0 / v;
+    S.dinv32[i] = (float)(1.0 / v);
+    S.dx[i] = 0.0;
+  }
+  double bn[1] = {0.0};
+  for (int i = t; i < S.nrow; i += NTB) bn[0] += S.rhs[i] * S.rhs[i];
+  block_sum<NTB>(bn);
+  const double bnorm = sqrt(bn[0]);
+  int iters = 0, outer = 0, status = 0;
+  double rel = 0.0;
+  if (bnorm > 0.0) {
+    for (outer = 0;; ++outer) {
+      double rr[1] = {0.0};
+      if (outer == 0) {
+        for (int i = t; i < S.nrow; i += NTB) {
+          S.r64[i] = S.rhs[i];
+          rr[0] += S.rhs[i] * S.rhs[i];
+        }
+      } else {
+        for (int bd = t; bd < S.s64.M; bd += NTB) body_gather(S.s64, plain<double>(S.dx), bd);
+        __syncthreads();
+        for (int c = t; c < n; c += NTB) contact_apply(S.s64, plain<double>(S.dx), S.q64, c);
+        __syncthreads();
+        for (int i = t; i < S.nrow; i += NTB) {
+          const double ri = S.rhs[i] - S.q64[i];
+          S.r64[i] = ri;
+          rr[0] += ri * ri;
+        }
+      }
+      block_sum<NTB>(rr);
+      const double rn = sqrt(rr[0]);
+      rel = rn / bnorm;
+      if (rel <= tol) break;
+      if (outer >= max_outer || iters >= maxit) {
+        status = 1;
+        break;
+      }
+      const double inv = 1.0 / rn;
+      for (int i = t; i < S.nrow; i += NTB) S.v32[i] = (float)(S.r64[i] * inv);
+      __syncthreads();
+      const int before = iters;
+      const int st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters);
+      const float* e = S.v32 + S.P;
+      for (int i = t; i < S.nrow; i += NTB) S.dx[i] += rn * (double)e[i];
+      __syncthreads();
+      if (st == 2 && iters == before) {
+        status = 2;
+        break;
+      }
+    }
+  }
+  if (t == 0) {
+    out[sid].iters = iters;
+    out[sid].outer = outer;
+    out[sid].status = status;
+    out[sid].rel = rel;
+  }
+}
+
 // ------------------------------------------------------------------ fused pipelined PCG
 // Contact partition: block g owns contacts [g*chunk, (g+1)*chunk) (Morton order,
 // so a chunk is spatially compact) and gathers every body its contacts touch
@@ -1508,18 +1729,7 @@ __global__ void k_diag(SysView<double> s, const double* __restrict__ H, double* 
     int u = (int)(i - c * s.slots);
     double v = 1.0;
     if (c < n && u < 3) {
-      double R[16];
-      load_rec(s.rec, (int)c, R);
-      double U0 = R[3 * u], U1 = R[3 * u + 1], U2 = R[3 * u + 2];
-      int a = s.ca[c], b = s.cb[c];
-      double t0 = R[13] * U2 - R[14] * U1, t1 = R[14] * U0 - R[12] * U2, t2 = R[12] * U1 - R[13] * U0;
-      v = s.inv_m[b] + s.inv_I[b] * (t0 * t0 + t1 * t1 + t2 * t2);
-      if (a < s.M) {
-        t0 = R[10] * U2 - R[11] * U1;
-        t1 = R[11] * U0 - R[9] * U2;
-        t2 = R[9] * U1 - R[10] * U0;
-        v += s.inv_m[a] + s.inv_I[a] * (t0 * t0 + t1 * t1 + t2 * t2);
-      }
+      v = diag_entry(s, (int)c, u);
       if (H) v += H[(u == 0 ? 0 : (u == 1 ? 3 : 5)) * n + c];
     }
     d64[i] = 1.0 / v;
@@ -2096,6 +2306,140 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   return st;
 }
 
+// Batched solve: build the scene table, order scenes by size, launch one
+// block per scene (block size given or measured), read the per-scene results.
+struct BatchRun {
+  std::vector<BatchScene> tab;
+  std::vector<int> order;
+};
+
+static void launch_batched(qp_ctx* c0, int nt, int n, const BatchScene* tab, const int* order, const qp_batch_opts* o,
+                           BatchOut* out) {
+  const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-3;
+  const int mo = o->max_outer > 0 ? o->max_outer : 50;
+  switch (nt) {
+    case 128: k_pcg_batched<128><<<n, 128, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
+    case 256: k_pcg_batched<256><<<n, 256, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
+    case 512: k_pcg_batched<512><<<n, 512, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
+    default: k_pcg_batched<1024><<<n, 1024, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
+  }
+  QP_CUDA(cudaGetLastError());
+}
+
+// measured block size per (device, batch size class)
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, long long>, int> g_tune;
+
+static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st, const double* const* rhs,
+                         double* const* dx, const qp_batch_opts* o, qp_solve_stats* stats, int* used) {
+  qp_ctx* c0 = ctxs[0];
+  std::vector<BatchScene> tab(n);
+  std::vector<std::pair<long long, int>> bysize(n);
+  long long work = 0;
+  for (int i = 0; i < n; ++i) {
+    qp_ctx* c = ctxs[i];
+    QP_REQUIRE(c, QP_INVALID_ARG, "newton_solve_batched: null context");
+    QP_REQUIRE(c->device == c0->device, QP_INVALID_ARG, "newton_solve_batched: contexts on different devices");
+    QP_REQUIRE(c->have_contacts, QP_NOT_READY, "newton_solve_batched: a context has no contacts");
+    QP_REQUIRE(rhs[i] && dx[i] && rhs[i] != dx[i], QP_INVALID_ARG, "newton_solve_batched: null or aliased vectors");
+    if (st && st[i]) QP_REQUIRE(st[i]->gamma && st[i]->lambda, QP_INVALID_ARG, "newton_solve_batched: bad state");
+    BatchScene& b = tab[i];
+    b.s64 = view64(c, true);
+    b.s32 = view32(c, true);
+    b.H64 = c->H.as<double>();
+    b.H32 = c->H32.as<float>();
+    b.dinv64 = c->dinv.as<double>();
+    b.dinv32 = c->dinv32.as<float>();
+    b.gamma = (st && st[i]) ? st[i]->gamma : nullptr;
+    b.lambda = (st && st[i]) ? st[i]->lambda : nullptr;
+    b.mu = c->mu;
+    b.rhs = rhs[i];
+    b.dx = dx[i];
+    const size_t P = (size_t)c->P;
+    double* w64 = static_cast<double*>(c->batch64.ensure(2 * P * sizeof(double)));
+    b.r64 = w64;
+    b.q64 = w64 + P;
+    b.v32 = static_cast<float*>(c->batch32.ensure(7 * P * sizeof(float)));
+    b.P = c->P;
+    b.nrow = c->slots * c->Nc;
+    bysize[i] = {-(long long)c->P - c->Nc, i};
+    work += c->P;
+  }
+  std::sort(bysize.begin(), bysize.end());
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = bysize[i].second;
+  // table, order and outputs in one device buffer of ctxs[0]
+  const size_t tb = sizeof(BatchScene) * n, ob = sizeof(int) * n, rb = sizeof(BatchOut) * n;
+  char* buf = static_cast<char*>(c0->batch_table.ensure(tb + 256 + ob + 256 + rb));
+  BatchScene* dtab = reinterpret_cast<BatchScene*>(buf);
+  int* dorder = reinterpret_cast<int*>(buf + ((tb + 255) / 256) * 256);
+  BatchOut* dout = reinterpret_cast<BatchOut*>(buf + ((tb + 255) / 256) * 256 + ((ob + 255) / 256) * 256);
+  // the other contexts' pending work (assembly, states) comes first
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i] != c0) {
+      QP_CUDA(cudaEventRecord(ctxs[i]->ev0, ctxs[i]->stream));
+      QP_CUDA(cudaStreamWaitEvent(c0->stream, ctxs[i]->ev0, 0));
+    }
+  QP_CUDA(cudaMemcpyAsync(dtab, tab.data(), tb, cudaMemcpyHostToDevice, c0->stream));
+  QP_CUDA(cudaMemcpyAsync(dorder, order.data(), ob, cudaMemcpyHostToDevice, c0->stream));
+  int nt = o->block_threads;
+  QP_REQUIRE(nt == 0 || nt == 128 || nt == 256 || nt == 512 || nt == 1024, QP_INVALID_ARG,
+             "newton_solve_batched: block_threads must be 0, 128, 256, 512 or 1024");
+  if (nt == 0) {
+    long long cls = 1;
+    while (cls < work / n) cls <<= 1;
+    const auto key = std::make_pair(c0->device, cls * 4096 + (n < 4096 ? n / 64 : 64));
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) nt = it->second;
+    }
+    if (nt == 0) {
+      float best = 1e30f;
+      for (int cand : {256, 512, 1024}) {
+        QP_CUDA(cudaEventRecord(c0->ev0, c0->stream));
+        launch_batched(c0, cand, n, dtab, dorder, o, dout);
+        QP_CUDA(cudaEventRecord(c0->ev1, c0->stream));
+        QP_CUDA(cudaEventSynchronize(c0->ev1));
+        float ms = 0;
+        QP_CUDA(cudaEventElapsedTime(&ms, c0->ev0, c0->ev1));
+        if (ms < best) {
+          best = ms;
+          nt = cand;
+        }
+      }
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = nt;
+    }
+  }
+  QP_CUDA(cudaEventRecord(c0->ev0, c0->stream));
+  launch_batched(c0, nt, n, dtab, dorder, o, dout);
+  QP_CUDA(cudaEventRecord(c0->ev1, c0->stream));
+  std::vector<BatchOut> res(n);
+  QP_CUDA(cudaMemcpyAsync(res.data(), dout, rb, cudaMemcpyDeviceToHost, c0->stream));
+  QP_CUDA(cudaStreamSynchronize(c0->stream));
+  float ms = 0;
+  QP_CUDA(cudaEventElapsedTime(&ms, c0->ev0, c0->ev1));
+  // later work on the other contexts waits for the batch
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i] != c0) QP_CUDA(cudaStreamWaitEvent(ctxs[i]->stream, c0->ev1, 0));
+  int rc = QP_OK;
+  for (int i = 0; i < n; ++i) {
+    const int code = res[i].status == 0 ? QP_OK : (res[i].status == 2 ? QP_BREAKDOWN : QP_NOT_CONVERGED);
+    if (stats) {
+      stats[i].status = code;
+      stats[i].iters = res[i].iters;
+      stats[i].outer = res[i].outer;
+      stats[i].rel_res = res[i].rel;
+      stats[i].ms = ms;
+      stats[i].fallback = 0;
+    }
+    if (rc == QP_OK && code != QP_OK) rc = code;
+  }
+  if (used) *used = nt;
+  return rc;
+}
+
 }  // namespace qp
 
 using namespace qp;
@@ -2178,6 +2522,16 @@ int newton_solve(qp_ctx_t c, const qp_state* st, const double* rhs, double* dx, 
   if (stats) *stats = s;
   if (s.status == QP_TIMEOUT) throw Error{QP_TIMEOUT, "newton_solve: device barrier wait expired"};
   return s.status;
+  API_END(c)
+}
+
+int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st, const double* const* rhs,
+                         double* const* dx, const qp_batch_opts* o, qp_solve_stats* stats, int* used) {
+  if (n < 1 || !ctxs || !ctxs[0] || !rhs || !dx || !o) return QP_INVALID_ARG;
+  qp_ctx* c = ctxs[0];
+  API_BEGIN(c)
+  QP_REQUIRE(o->tol > 0 && o->maxit > 0, QP_INVALID_ARG, "newton_solve_batched: tol > 0 and maxit > 0 required");
+  return batched_solve(n, ctxs, st, rhs, dx, o, stats, used);
   API_END(c)
 }
 

@@ -1,0 +1,89 @@
+"""GPU parity: many independent Newton systems in one launch (one thread block
+per scene) against the oracle's Schur matrices and the single-scene solver."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import Problem, relerr, to_np
+from oracle import qp
+from paper_1808_02558_gb300 import binding
+from synth import Scene, lattice_scene
+from test_gpu_newton import interior_point
+from test_oracle_qp import sphere_on_plane
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return binding.Context()
+
+
+def scenes():
+    out = [lattice_scene(n, 10 + n, polydisperse=(n % 2 == 1), mu=0.2 + 0.1 * n) for n in (2, 3, 4, 5, 6)]
+    out += [lattice_scene(3, 40, mu=0.8), sphere_on_plane((0.3, 0.1, -0.2)),
+            Scene(name="free", pos=[[0.0, 0.0, 3.0]], vel=[[0.0, 0.0, 0.0]], omega=[[0.0, 0.0, 0.0]], radius=[0.5])]
+    return out
+
+
+@pytest.mark.parametrize("block", [256, 0])
+def test_batched_solves_match_oracle_and_single(ctx, block):
+    pbs, states, rhs, dx, keep = [], [], [], [], []
+    for i, s in enumerate(scenes()):
+        pb = Problem(ctx, s)
+        g, lam = interior_point(pb, i) if pb.Nc > 0 else (np.zeros(0), np.zeros(0))
+        gd, ld, st = pb.state(g, lam) if pb.Nc > 0 else (None, None, None)
+        r = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+        if st is not None:
+            pb.ctx.newton_rhs(st, r)
+        else:
+            r.zero_()
+        pbs.append((pb, g, lam))
+        states.append(st)
+        rhs.append(r)
+        dx.append(torch.full_like(r, 9.0))
+        keep.append((gd, ld))
+    stats, used = binding.newton_solve_batched([p[0].ctx for p in pbs], states, rhs, dx, tol=1e-10,
+                                               block_threads=block, allow=())
+    assert used in (256, 512, 1024)
+    for (pb, g, lam), st, r, x, s in zip(pbs, states, rhs, dx, stats):
+        assert s.status == binding.QP_OK
+        if pb.Nc == 0:
+            assert torch.count_nonzero(x).item() == 0 and s.iters == 0
+            continue
+        S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+        b = pb.unpad(to_np(r))
+        xs = pb.unpad(to_np(x))
+        assert np.linalg.norm(b - S @ xs) <= 1.05e-10 * np.linalg.norm(b)
+        assert s.rel_res <= 1e-10
+        assert np.all(to_np(x)[3 * pb.Nc:] == 0.0)
+        one = torch.empty_like(r)
+        pb.ctx.newton_solve(st, r, one, pb.ctx.solve_opts(tol=1e-10, maxit=100000, mixed=1, inner_tol=1e-3,
+                                                          max_outer=60), allow=())
+        assert relerr(xs, pb.unpad(to_np(one))) <= 1e-8
+
+
+def test_batched_without_state_is_plain_N(ctx):
+    s = sphere_on_plane((0.3, 0.1, -0.2))
+    pb = Problem(ctx, s)
+    b = torch.tensor([1.0, -2.0, 0.5, 0.0], dtype=torch.float64, device="cuda")
+    x = torch.empty_like(b)
+    stats, _ = binding.newton_solve_batched([pb.ctx], [None], [b], [x], tol=1e-12, block_threads=128, allow=())
+    m = s.mass[0]
+    want = np.array([1.0 * m, -2.0 * m / 3.5, 0.5 * m / 3.5])  # N = diag(1/m, 3.5/m, 3.5/m)
+    assert np.allclose(to_np(x)[:3], want, rtol=1e-10, atol=0)
+    assert to_np(x)[3] == 0.0
+
+
+def test_batched_rejects_bad_arguments(ctx):
+    pb = Problem(ctx, sphere_on_plane((0.3, 0.1, -0.2)))
+    b = torch.ones(pb.P, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.QPError) as e:
+        binding.newton_solve_batched([pb.ctx], [None], [b], [b], tol=1e-8, allow=())
+    assert e.value.code == binding.QP_INVALID_ARG
+    x = torch.empty_like(b)
+    with pytest.raises(binding.QPError) as e:
+        binding.newton_solve_batched([pb.ctx], [None], [b], [x], tol=1e-8, block_threads=100, allow=())
+    assert e.value.code == binding.QP_INVALID_ARG
