@@ -438,7 +438,7 @@ def batched_leg(args, binding, workload):
         states.append(st)
         rhs.append(r)
         dx.append(torch.empty_like(r))
-        keep.append((g, lam))
+        keep.append((g, lam, con.Nc, con.M))
         nc_tot += con.Nc
         p_tot += con.P
     torch.cuda.synchronize()
@@ -461,12 +461,19 @@ def batched_leg(args, binding, workload):
     torch.cuda.synchronize()
     t_s = time.perf_counter() - t0
     tb = statistics.median(t_b)
+    # algorithmic bytes of all solves (same per-scene count as the single-scene kernel)
+    nbytes = sum(solve_bytes(k[2], k[3], 3 * k[2], s.iters, s.outer) for k, s in zip(keep, stats))
+    hbm, src = peaks()
+    ach = nbytes / (stats[0].ms / 1e3) / 1e9
     out = {"scenes": n, "sides": "U{4..16}", "mu": "U[0.2, 0.8]", "contacts": nc_tot, "padded_unknowns": p_tot,
            "block_threads": used, "tol": 1e-8, "batched_ms": tb * 1e3, "batched_device_ms": stats[0].ms,
            "batched_solves_per_s": n / tb, "sequential_ms": t_s * 1e3, "sequential_solves_per_s": n / t_s,
            "speedup": t_s / tb, "max_rel_res": max(s.rel_res for s in stats),
            "not_converged": sum(1 for s in stats if s.status != binding.QP_OK),
-           "iters_mean": statistics.mean(s.iters for s in stats)}
+           "iters_mean": statistics.mean(s.iters for s in stats),
+           "roofline": {"kernel": "k_pcg_batched", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "peak_source": src, "bytes": nbytes,
+                        "time": "device time of the launch (events)"}}
     for c in ctxs:
         c.close()
     return out
