@@ -133,3 +133,24 @@ def test_pdip_solve_sphere_on_plane_and_cap(ctx):
     pb.ctx.pdip_init(st2, 1.0)
     stats2, n2 = pb.ctx.pdip_solve(st2, gpu_opts(pb.ctx), gap_tol=1e-12, dual_tol=1e-9, max_iter=2)
     assert stats2.status == binding.QP_NOT_CONVERGED and n2 == 2
+
+
+def test_full_size_step_matches_oracle(ctx):
+    """One PDIP iteration on the 40^3 pile (2^20 padded unknowns) in the launch
+    configuration of the benchmark (FP32 inner PCG + FP64 refinement to 1e-8)
+    against the oracle's iteration with its own Jacobi-PCG Newton solve."""
+    pb = Problem(ctx, scene_for("pile40p", 1))
+    mu = pb.scene.mu
+    g0, l0 = qp.initial_point(pb.Nc, mu)
+    g1, l1, info = pdip.pdip_step(pb.N, pb.r, mu, g0, l0, method="pcg")
+    gd, ld, st = pb.state(g0, l0)
+    opts = pb.ctx.pdip_opts(pb.ctx.solve_opts(tol=1e-8, maxit=200000, mixed=1, inner_tol=1e-3, max_outer=60))
+    stats = pb.ctx.pdip_step(st, opts, allow=())
+    assert abs(stats.eta - info.eta) <= 1e-12 * info.eta
+    assert abs(stats.t - info.t) <= 1e-12 * info.t
+    assert abs(stats.r_t - info.r_t_norm) <= 1e-10 * info.r_t_norm
+    assert stats.halvings == info.halvings
+    assert abs(stats.s - info.s) <= 1e-6 * info.s
+    assert stats.solve.rel_res <= 1e-8
+    assert relerr(pb.unpad(to_np(gd)), g1) <= 1e-6
+    assert relerr(to_np(ld), l1) <= 1e-6
