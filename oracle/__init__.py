@@ -12,6 +12,7 @@ Modules
   krylov   : Jacobi-preconditioned CG                           (Sec. 3.3, 4.2)
   tt       : TT-SVD, rounding, QTT tensorisation and mat-vec    (Sec. 3.1, 3.2)
   timestep : velocity/position update, warm start of the PDIP   (Sec. 2.3, 3.3)
+  mpnn     : message-passing network of the learned warm start (extension)
 
 Parity status per function is stated in each module header; functions with no
 independent pin say "parity unpinned" there.
