@@ -269,6 +269,44 @@ int pdip_measure(qp_ctx_t ctx, const qp_state* st, double* eta_host, double* r_d
 int pdip_solve(qp_ctx_t ctx, qp_state* st, const qp_pdip_opts* opts, double gap_tol, double dual_tol, int max_iter,
                qp_pdip_stats* stats, int* iters_host);
 
+/* ---- Learned warm start (an extension; the paper has no counterpart) ---- */
+
+/* A message-passing network over the contact graph predicts the impulses the
+ * PDIP starts from.  Contacts are the nodes; a message goes from a contact to
+ * each of its dynamic bodies and back: m_b = sum of h_c over the contacts of
+ * body b, s_c = m_a + m_b (the static floor sends nothing).  With x_c the 8
+ * scaled features of contact c (normal n in the world frame, Phi/dt, the
+ * relative velocity D_c^T v in the contact frame = r_c - b_c, mu; each times
+ * feat_scale[k]):
+ *   h0 = relu(W0 x + b0), hl = relu(Wl [h(l-1); s(h(l-1))] + bl), l = 1..3,
+ *   o = Wo h3 + bo  (o = impulse / out_scale).
+ * params: device float[QP_MPNN_NPARAM], the FP32 master vector [W0 (64x8),
+ * b0, W1 (64x128), b1, W2, b2, W3, b3, Wo (3x64), bo], row-major; the passes
+ * use its BF16 rounding and FP32 arithmetic.  Activations live in the
+ * context (valid until its next mpnn_* call).                               */
+#define QP_MPNN_NPARAM 25539
+
+/* out: device float[3*Nc], the network outputs for the current contacts.     */
+int mpnn_forward(qp_ctx_t ctx, const float* params, const float* feat_scale_host, float* out);
+
+/* Loss = mean over the 3 Nc entries of (o - target)^2 (target: device
+ * float[3*Nc], impulses / out_scale); grad: device float[QP_MPNN_NPARAM]
+ * (overwritten) = d loss / d params at the BF16-rounded parameters;
+ * *loss_host (may be NULL) after an internal synchronisation.
+ * QP_INVALID_ARG without contacts.                                           */
+int mpnn_grad(qp_ctx_t ctx, const float* params, const float* feat_scale_host, const float* target, float* grad,
+              double* loss_host);
+
+/* One Adam step (Kingma and Ba, 2015) on the FP32 master parameters: m, v
+ * device float[QP_MPNN_NPARAM] moment buffers (zero before step 1), step >= 1. */
+int mpnn_adam(qp_ctx_t ctx, float* params, float* m, float* v, const float* grad, int step, double lr, double beta1,
+              double beta2, double eps);
+
+/* Warm start from network outputs: gamma = out_scale * o moved into the
+ * cone's interior (gamma_n >= gn_min, |gamma_t| <= shrink mu gamma_n),
+ * dummies 0, lambda_i = -1/f_i (centred at t = 1), t = 1.                   */
+int mpnn_warm_start(qp_ctx_t ctx, qp_state* st, const float* out, double out_scale, double gn_min, double shrink);
+
 /* ---- QTT matrices (Sec. 3.1-3.2) --------------------------------------- */
 
 /* Core k (k = 0..d-1) of a QTT matrix is G_k(a, i, j, b), a < r_k, b <

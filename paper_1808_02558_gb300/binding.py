@@ -25,7 +25,7 @@ QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
            "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
-           "ccp_advance", "qtt_from_host",
+           "ccp_advance", "mpnn_forward", "mpnn_grad", "mpnn_adam", "mpnn_warm_start", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
 
@@ -110,6 +110,10 @@ def load(path: str = LIB_PATH):
         "newton_solve_batched": (i, [i, C.POINTER(vp), C.POINTER(C.POINTER(State)), C.POINTER(vp), C.POINTER(vp),
                                      C.POINTER(BatchOpts), C.POINTER(SolveStats), C.POINTER(i)]),
         "ccp_advance": (i, [vp, C.POINTER(Scene), C.POINTER(State), vp, vp, vp]),
+        "mpnn_forward": (i, [vp, vp, C.POINTER(C.c_float), vp]),
+        "mpnn_grad": (i, [vp, vp, C.POINTER(C.c_float), vp, vp, C.POINTER(d)]),
+        "mpnn_adam": (i, [vp, vp, vp, vp, vp, i, d, d, d, d]),
+        "mpnn_warm_start": (i, [vp, C.POINTER(State), vp, d, d, d]),
         "qtt_from_host": (i, [vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(vp)]),
         "qtt_free": (i, [vp, vp]),
         "qtt_get_dims": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
@@ -251,6 +255,27 @@ class Context:
         sc, dev = self.scene
         self._check(self.lib.ccp_advance(self.h, C.byref(sc), C.byref(st), _ptr(dev["pos"]), _ptr(dev["vel"]),
                                          _ptr(dev["omega"])), "ccp_advance")
+
+    # ------------------------------------------------------------- learned warm start
+    def mpnn_forward(self, params, feat_scale, out):
+        sc = (C.c_float * 8)(*[float(v) for v in feat_scale])
+        self._check(self.lib.mpnn_forward(self.h, _ptr(params), sc, _ptr(out) if out.numel() else None),
+                    "mpnn_forward")
+
+    def mpnn_grad(self, params, feat_scale, target, grad) -> float:
+        sc = (C.c_float * 8)(*[float(v) for v in feat_scale])
+        loss = C.c_double(0.0)
+        self._check(self.lib.mpnn_grad(self.h, _ptr(params), sc, _ptr(target), _ptr(grad), C.byref(loss)),
+                    "mpnn_grad")
+        return loss.value
+
+    def mpnn_adam(self, params, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.mpnn_adam(self.h, _ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr),
+                                       float(beta1), float(beta2), float(eps)), "mpnn_adam")
+
+    def mpnn_warm_start(self, st: State, out, out_scale, gn_min=1e-3, shrink=0.9):
+        self._check(self.lib.mpnn_warm_start(self.h, C.byref(st), _ptr(out) if out.numel() else None,
+                                             float(out_scale), float(gn_min), float(shrink)), "mpnn_warm_start")
 
     def pdip_init_warm(self, st: State, prev_a, prev_b, prev_gamma, prev_slots=3, gn0=1.0, shrink=0.9):
         """Warm start from the previous step's pairs and impulses (device tensors

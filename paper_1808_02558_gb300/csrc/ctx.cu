@@ -121,7 +121,7 @@ int qp_destroy(qp_ctx_t c) {
                  &c->rec64, &c->rec32, &c->inv_m, &c->inv_I, &c->inv_m32, &c->inv_I32,
                  &c->bptr, &c->inc, &c->wbody, &c->wbody32, &c->H, &c->H32, &c->dinv, &c->dinv32,
                  &c->partial, &c->ctl, &c->part_nb, &c->part_bodies, &c->part_cl, &c->fused_pool, &c->batch64, &c->batch32,
-                 &c->batch_table};
+                 &c->batch_table, &c->mp_act, &c->mp_w, &c->mp_grad, &c->mp_sum};
   for (Buf* b : bufs) b->release();
   for (auto& b : c->v64) b.release();
   for (auto& b : c->v32) b.release();

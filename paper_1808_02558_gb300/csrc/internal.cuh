@@ -103,6 +103,7 @@ struct qp_ctx {
   int part_G = 0, part_chunk = 0, part_maxb = 0, part_nbmax = 0;
   qp::Buf part_nb, part_bodies, part_cl;
   qp::Buf fused_pool;
+  qp::Buf mp_act, mp_w, mp_grad, mp_sum;  // learned warm start: activations, BF16 weights, scratch
   qp::Buf batch64, batch32, batch_table;  // batched solves: per-scene vectors; table (first context)  // records of the fused pipelined solver (never shared with the classic solver)
 };
 
