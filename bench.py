@@ -371,6 +371,7 @@ def run_ours(args):
 
     ts_out = time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream) if args.ts_steps > 0 else None
     batch_out = batched_leg(args, binding, workload) if args.batch_scenes > 0 else None
+    learned_out = learned_leg(args, binding, workload) if args.learned_steps > 0 else None
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -396,6 +397,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "time_stepping": ts_out,
         "batched": batch_out,
+        "learned_warm_start": learned_out,
     }
     if rank == 0 and not args.no_cpu_baseline:
         ctx.pdip_init(st, 1.0)
@@ -408,6 +410,83 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def learned_leg(args, binding, workload):
+    """Learned warm start: the network is trained on the PDIP iterates the
+    library itself produces (12 iterations from the cold start) on 8^3 piles of
+    seeds 2..9, then starts the PDIP of the unseen seed 1 (cold start as the
+    fallback); reported: the surrogate gap and dual residual after each of 12
+    PDIP iterations from the cold and the learned start."""
+    import torch
+
+    from paper_1808_02558_gb300 import learned
+    from synth import scene_for
+
+    K = 12
+
+    def system(seed):
+        sc = scene_for("pile8", seed)
+        c = binding.Context()
+        _, con = workload.assemble(c, sc)
+        g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+        return c, con, g, lam, c.state(g, lam)
+
+    opts_of = lambda c: c.pdip_opts(c.solve_opts(tol=1e-10, maxit=200000))
+    ok = (binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL)
+    train = []
+    for seed in range(2, 10):
+        c, con, g, lam, st = system(seed)
+        c.pdip_init(st, 1.0)
+        o = opts_of(c)
+        for _ in range(K):
+            c.pdip_step(st, o, allow=ok)
+        idx = torch.arange(con.Nc, device="cuda")
+        rows = (3 * idx[:, None] + torch.arange(3, device="cuda")[None, :]).reshape(-1)
+        train.append((c, g[rows].clone()))
+    scale = [1.0, 1.0, 1.0, 0.05, 5.0, 5.0, 5.0, 2.0]
+    out_scale = float(torch.cat([t[0::3] for _, t in train]).mean())
+    net = learned.WarmStartNet(11, scale, out_scale)
+    t0 = time.perf_counter()
+    losses = []
+    for _ in range(args.learned_steps):
+        for c, t in train:
+            losses.append(net.train_step(c, t, 1e-3))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    def trajectory(c, st):
+        o = opts_of(c)
+        hist = []
+        for _ in range(K):
+            c.pdip_step(st, o, allow=ok)
+            hist.append(c.pdip_measure(st))
+        return hist
+
+    c, con, g, lam, st = system(1)
+    c.pdip_init(st, 1.0)
+    cold0 = c.pdip_measure(st)
+    cold = trajectory(c, st)
+    gn_min = 1e-3 * out_scale
+    used, _, start0 = net.start(c, st, con.Nc, gn_min=gn_min)
+    policy = trajectory(c, st)
+    net.warm_start(c, st, con.Nc, gn_min)  # the learned start without the fallback
+    forced = trajectory(c, st)
+    target_gap = cold[-1][0]
+    reach = next((i + 1 for i, (e, _) in enumerate(forced) if e <= target_gap), None)
+    for cc, _ in train:
+        cc.close()
+    c.close()
+    return {"train": {"scenes": "pile8 seeds 2..9", "targets": f"PDIP iterate {K} from the cold start",
+                      "steps": len(losses), "first_loss": losses[0], "final_loss": losses[-1],
+                      "seconds": t_train, "out_scale": out_scale},
+            "eval": {"scene": "pile8 seed 1 (unseen)", "start_used": used,
+                     "cold_start": {"eta": cold0[0], "r_dual": cold0[1]},
+                     "learned_start": {"eta": start0[0], "r_dual": start0[1]},
+                     "cold_eta_r_dual": cold, "with_fallback_eta_r_dual": policy,
+                     "learned_forced_eta_r_dual": forced,
+                     "learned_forced_iters_to_cold_final_gap": reach}}
 
 
 def batched_leg(args, binding, workload):
@@ -636,6 +715,7 @@ def main():
     ap.add_argument("--qtt-steps", type=int, default=1, help="PDIP steps of the QTT-PCG comparison leg (0: skip)")
     ap.add_argument("--ts-steps", type=int, default=3, help="time steps of the time-stepping leg (0: skip)")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
+    ap.add_argument("--learned-steps", type=int, default=200, help="training epochs of the learned leg (0: skip)")
     ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],
                     help="Krylov method of the QTT leg (the paper uses BiCGSTAB)")
     ap.add_argument("--qtt-maxit", type=int, default=2000,

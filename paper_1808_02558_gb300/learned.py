@@ -55,3 +55,18 @@ class WarmStartNet:
 
     def warm_start(self, ctx: binding.Context, st: binding.State, Nc: int, gn_min: float, shrink: float = 0.9):
         ctx.mpnn_warm_start(st, self.predict(ctx, Nc), self.out_scale, gn_min, shrink)
+
+    def start(self, ctx: binding.Context, st: binding.State, Nc: int, gn_min: float, shrink: float = 0.9):
+        """PDIP start with the cold start as the fallback: the network's warm start
+        is kept when its dual residual is below the cold start's, else the cold
+        start is used.  Returns ("learned" or "cold", (eta, r_dual) of the cold
+        start, (eta, r_dual) of the learned start)."""
+        ctx.pdip_init(st, 1.0)
+        cold = ctx.pdip_measure(st)
+        self.warm_start(ctx, st, Nc, gn_min, shrink)
+        warm = ctx.pdip_measure(st)
+        if math.isfinite(warm[1]) and warm[1] < cold[1]:
+            return "learned", cold, warm
+        ctx.pdip_init(st, 1.0)
+        return "cold", cold, warm
+

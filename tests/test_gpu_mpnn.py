@@ -100,3 +100,21 @@ def test_training_fits_pdip_iterates(ctx):
             net.train_step(pb.ctx, t, 1e-3)
     last = [net.train_step(pb.ctx, t, 1e-3) for pb, t in data]
     assert max(last) <= 0.2 * min(first)
+
+
+def test_start_never_worse_than_cold(ctx):
+    """net.start keeps the learned start only when its dual residual is below the
+    cold start's; an untrained network falls back to the cold start exactly."""
+    pb = Problem(ctx, scene_for("pile8", 1))
+    g = torch.zeros(pb.P, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(2 * pb.Nc, dtype=torch.float64, device="cuda")
+    st = pb.ctx.state(g, lam)
+    pb.ctx.pdip_init(st, 1.0)
+    _, rd_cold = pb.ctx.pdip_measure(st)
+    g0 = g.clone()
+    net = learned.WarmStartNet(3, SCALE, out_scale=1e4)  # wildly scaled: far from the cold start
+    used, cold, warm = net.start(pb.ctx, st, pb.Nc, gn_min=1.0)
+    _, rd = pb.ctx.pdip_measure(st)
+    assert rd <= rd_cold and cold[1] == rd_cold
+    if used == "cold":
+        assert torch.equal(g, g0)
