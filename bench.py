@@ -570,6 +570,7 @@ def time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream):
     dev_s = workload.scene_to_device(scene, "cuda")
     rows, prev = [], None
     for step in range(args.ts_steps):
+        dev_before = {k: v.clone() for k, v in dev_s.items()}  # this step's scene (for the fresh-context refresh)
         flush.zero_()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
@@ -604,10 +605,31 @@ def time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream):
         ev[3].synchronize()
         keys = set(zip(ab[0].tolist(), ab[1].tolist()))
         persist = None if prev is None else len(keys & prev[3]) / max(1, len(keys))
+        # QTT refresh of the first Newton system of the step (compress + invert):
+        # warm-started by the previous step's inverse in this context, and from
+        # scratch in a fresh context (the reuse speed-up across time steps)
+        qtt_ms = None
+        if args.ts_qtt:
+            def refresh_ms(c):
+                g3 = torch.zeros_like(g)
+                l3 = torch.zeros_like(lam)
+                s3 = c.state(g3, l3)
+                c.pdip_init(s3, 1.0)
+                so = c.solve_opts(binding.QP_QTT_PCG, None, tol=1e-8, maxit=args.qtt_maxit, mixed=1,
+                                  inner_tol=1e-3, max_outer=60, core_dtype=binding.QP_BF16)
+                po = c.pdip_opts(so, qtt_refresh=1, qtt_eps=args.qtt_eps, qtt_rmax=args.qtt_rmax)
+                return c.pdip_step(s3, po, allow=ok).ms_refresh
+            warm_ms = refresh_ms(ctx)
+            fresh = binding.Context()
+            fresh.assemble(dev_before, scene.floor_z, scene.gravity, scene.dt, scene.delta, scene.mu, 3)
+            cold_ms = refresh_ms(fresh)
+            fresh.close()
+            qtt_ms = {"refresh_ms_reusing_previous": warm_ms if step > 0 else None, "refresh_ms_from_scratch": cold_ms}
         rows.append({"step": step, "contacts": con.Nc, "persisting": persist,
                      "ms_assemble": ev[0].elapsed_time(ev[1]), "ms_pdip_window": ev[1].elapsed_time(ev[2]),
                      "ms_advance": ev3.elapsed_time(ev[3]), "eta": eta, "r_dual": rd,
-                     "cold_eta": None if cold is None else cold[0], "cold_r_dual": None if cold is None else cold[1]})
+                     "cold_eta": None if cold is None else cold[0], "cold_r_dual": None if cold is None else cold[1],
+                     "qtt": qtt_ms})
         prev = (ab[0], ab[1], g.clone(), keys)
     ctx.close()
     ms = [r["ms_assemble"] + r["ms_pdip_window"] + r["ms_advance"] for r in rows]
@@ -714,6 +736,7 @@ def main():
     ap.add_argument("--qtt-rmax", type=int, default=10)
     ap.add_argument("--qtt-steps", type=int, default=1, help="PDIP steps of the QTT-PCG comparison leg (0: skip)")
     ap.add_argument("--ts-steps", type=int, default=3, help="time steps of the time-stepping leg (0: skip)")
+    ap.add_argument("--ts-qtt", type=int, default=1, help="time-stepping leg: measure the QTT refresh reuse (0: skip)")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
     ap.add_argument("--learned-steps", type=int, default=200, help="training epochs of the learned leg (0: skip)")
     ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],
