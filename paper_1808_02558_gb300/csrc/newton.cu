@@ -1151,14 +1151,31 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
     if (!(pq > 0.f)) return 2;
     const float alpha = rz / pq;
     float a2[2] = {0.f, 0.f};
-    for (int i = t; i < nrow; i += NTB) {
-      e[i] += alpha * pnew[i];
-      const float ri = r[i] - alpha * q[i];
-      r[i] = ri;
-      const float zi = dinv[i] * ri;
-      z[i] = zi;
-      a2[0] += ri * ri;
-      a2[1] += ri * zi;
+    // four rows per thread and pass, every load of the pass before any store
+    for (int i0 = t; i0 < nrow; i0 += 4 * NTB) {
+      float pv[4], ev[4], rv[4], qv[4], dv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j * NTB;
+        const bool in = i < nrow;
+        pv[j] = in ? pnew[i] : 0.f;
+        ev[j] = in ? e[i] : 0.f;
+        rv[j] = in ? r[i] : 0.f;
+        qv[j] = in ? q[i] : 0.f;
+        dv[j] = in ? dinv[i] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j * NTB;
+        if (i >= nrow) break;
+        e[i] = ev[j] + alpha * pv[j];
+        const float ri = rv[j] - alpha * qv[j];
+        r[i] = ri;
+        const float zi = dv[j] * ri;
+        z[i] = zi;
+        a2[0] += ri * ri;
+        a2[1] += ri * zi;
+      }
     }
     block_sum<NTB>(a2);
     ++iters;
