@@ -269,6 +269,15 @@ int pdip_measure(qp_ctx_t ctx, const qp_state* st, double* eta_host, double* r_d
 int pdip_solve(qp_ctx_t ctx, qp_state* st, const qp_pdip_opts* opts, double gap_tol, double dual_tol, int max_iter,
                qp_pdip_stats* stats, int* iters_host);
 
+/* Failure-detection self-test of the bounded grid barrier of the persistent
+ * kernels (no paper counterpart): one cooperative launch (one 128-thread block
+ * per SM) in which block absent_block never arrives; every other block's wait
+ * expires after `budget` clock ticks and records QP_TIMEOUT, which is written
+ * to *device_status (absent_block < 0: all arrive, status QP_OK).  The launch
+ * always ends; the context stays usable.  QP_INVALID_ARG unless 0 < budget <=
+ * the kernels' own budget (4e9 ticks) and absent_block < the SM count.       */
+int qp_selftest_barrier(qp_ctx_t ctx, long long budget, int absent_block, int* device_status);
+
 /* ---- Learned warm start (an extension; the paper has no counterpart) ---- */
 
 /* A message-passing network over the contact graph predicts the impulses the

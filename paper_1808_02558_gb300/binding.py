@@ -25,7 +25,7 @@ QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
            "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
-           "ccp_advance", "mpnn_forward", "mpnn_grad", "mpnn_adam", "mpnn_warm_start", "qtt_from_host",
+           "ccp_advance", "qp_selftest_barrier", "mpnn_forward", "mpnn_grad", "mpnn_adam", "mpnn_warm_start", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "newton_solve_batched": (i, [i, C.POINTER(vp), C.POINTER(C.POINTER(State)), C.POINTER(vp), C.POINTER(vp),
                                      C.POINTER(BatchOpts), C.POINTER(SolveStats), C.POINTER(i)]),
         "ccp_advance": (i, [vp, C.POINTER(Scene), C.POINTER(State), vp, vp, vp]),
+        "qp_selftest_barrier": (i, [vp, ll, i, C.POINTER(i)]),
         "mpnn_forward": (i, [vp, vp, C.POINTER(C.c_float), vp]),
         "mpnn_grad": (i, [vp, vp, C.POINTER(C.c_float), vp, vp, C.POINTER(d)]),
         "mpnn_adam": (i, [vp, vp, vp, vp, vp, i, d, d, d, d]),
@@ -255,6 +256,13 @@ class Context:
         sc, dev = self.scene
         self._check(self.lib.ccp_advance(self.h, C.byref(sc), C.byref(st), _ptr(dev["pos"]), _ptr(dev["vel"]),
                                          _ptr(dev["omega"])), "ccp_advance")
+
+    def selftest_barrier(self, budget: int, absent_block: int) -> int:
+        """Device status of a cooperative launch in which one block skips the grid barrier."""
+        status = C.c_int(0)
+        self._check(self.lib.qp_selftest_barrier(self.h, int(budget), int(absent_block), C.byref(status)),
+                    "qp_selftest_barrier")
+        return status.value
 
     # ------------------------------------------------------------- learned warm start
     def mpnn_forward(self, params, feat_scale, out):

@@ -1990,6 +1990,15 @@ __global__ void k_advance(SysView<double> s, const double* __restrict__ gamma, c
   }
 }
 
+// Bounded-wait self-test: block `absent` never arrives at the grid barrier, so
+// every other block's wait runs out after `budget` clock ticks and records
+// QP_TIMEOUT (absent < 0: all arrive, no error).  Nothing hangs either way.
+__global__ void k_barrier_probe(DevCtl* ctl, long long budget, int absent) {
+  barrier_init();
+  if ((int)blockIdx.x == absent) return;
+  grid_barrier(ctl, gridDim.x, budget);
+}
+
 template <class K>
 int coop_grid(qp_ctx* c, K kernel) {
   int per_sm = 0;
@@ -2549,6 +2558,21 @@ int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
   API_BEGIN(c)
   QP_REQUIRE(o->tol > 0 && o->maxit > 0, QP_INVALID_ARG, "newton_solve_batched: tol > 0 and maxit > 0 required");
   return batched_solve(n, ctxs, st, rhs, dx, o, stats, used);
+  API_END(c)
+}
+
+int qp_selftest_barrier(qp_ctx_t c, long long budget, int absent_block, int* device_status) {
+  API_BEGIN(c)
+  QP_REQUIRE(budget > 0 && budget <= BARRIER_BUDGET && device_status, QP_INVALID_ARG,
+             "qp_selftest_barrier: need 0 < budget <= the default budget and a status pointer");
+  QP_REQUIRE(absent_block < c->num_sms, QP_INVALID_ARG, "qp_selftest_barrier: absent block out of range");
+  ensure_partial(c);
+  reset_ctl(c);
+  DevCtl* ctl = c->ctl.as<DevCtl>();
+  void* args[] = {&ctl, &budget, &absent_block};
+  QP_CUDA(cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(c->num_sms), dim3(128), args, 0, c->stream));
+  DevCtl h = read_ctl(c);
+  *device_status = h.err;
   API_END(c)
 }
 
