@@ -231,7 +231,11 @@ typedef struct {
                          (D = diag S) and invert it before the solve; the
                          preconditioner is D^-1/2 X~ D^-1/2.  The new inverse
                          is kept by the context and warm-starts the next
-                         refresh (solve.X, when set, is the warm start)        */
+                         refresh (solve.X, when set, is the warm start).
+                         0 with a QTT preconditioner and solve.X NULL: reuse
+                         the context's last refreshed inverse (re-use across
+                         Newton iterations, Sec. 3.3); QP_INVALID_ARG if
+                         there is none of this size                          */
   double qtt_eps;     /* TT accuracy of the refresh                            */
   int qtt_rmax;       /* TT rank cap of the refresh                            */
 } qp_pdip_opts;

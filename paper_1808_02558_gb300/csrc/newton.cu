@@ -2625,6 +2625,11 @@ int pdip_step(qp_ctx_t c, qp_state* st, const qp_pdip_opts* o, qp_pdip_stats* st
     QP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     out.ms_refresh = ms;
     so.X = X;
+  } else if (so.precond == QP_QTT_PCG && !so.X) {
+    // no refresh and no X: reuse the inverse of the context's last refresh
+    QP_REQUIRE(c->last_inv && c->last_inv->d == c->L, QP_INVALID_ARG,
+               "pdip_step: QTT preconditioner without X, and no refreshed inverse of this size to reuse");
+    so.X = c->last_inv;
   }
   PdipArgs A = pdip_args(c, st);
   A.nu = o->nu;

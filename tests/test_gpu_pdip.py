@@ -154,3 +154,21 @@ def test_full_size_step_matches_oracle(ctx):
     assert stats.solve.rel_res <= 1e-8
     assert relerr(pb.unpad(to_np(gd)), g1) <= 1e-6
     assert relerr(to_np(ld), l1) <= 1e-6
+
+
+def test_qtt_inverse_reuse_across_newton_iterations(ctx):
+    """qtt_refresh = 0 without X reuses the context's last refreshed inverse
+    (Sec. 3.3 re-use); with nothing refreshed yet it is an invalid argument."""
+    pb = Problem(ctx, scene_for("pile8", 2))
+    g, lam = pb.oracle_iterates(2)
+    gd, ld, st = pb.state(g, lam)
+    so = pb.ctx.solve_opts(binding.QP_QTT_PCG, None, tol=1e-10, maxit=20000)
+    with pytest.raises(binding.QPError) as e:
+        pb.ctx.pdip_step(st, pb.ctx.pdip_opts(so, qtt_refresh=0), allow=())
+    assert e.value.code == binding.QP_INVALID_ARG
+    s1 = pb.ctx.pdip_step(st, pb.ctx.pdip_opts(so, qtt_refresh=1, qtt_eps=1e-2, qtt_rmax=10), allow=())
+    assert s1.ms_refresh > 0
+    g2, l2, _ = pdip.pdip_step(pb.N, pb.r, pb.scene.mu, *pb.oracle_iterates(3))
+    s2 = pb.ctx.pdip_step(st, pb.ctx.pdip_opts(so, qtt_refresh=0), allow=())
+    assert s2.ms_refresh == 0 and s2.solve.rel_res <= 1e-10
+    assert relerr(pb.unpad(to_np(gd)), g2) <= 1e-7
