@@ -28,11 +28,11 @@ def scenes():
     return out
 
 
-@pytest.mark.parametrize("block", [256, 0])
-def test_batched_solves_match_oracle_and_single(ctx, block):
+@pytest.mark.parametrize("block,slots", [(256, 3), (0, 3), (512, 4)])
+def test_batched_solves_match_oracle_and_single(ctx, block, slots):
     pbs, states, rhs, dx, keep = [], [], [], [], []
     for i, s in enumerate(scenes()):
-        pb = Problem(ctx, s)
+        pb = Problem(ctx, s, slots=slots)
         g, lam = interior_point(pb, i) if pb.Nc > 0 else (np.zeros(0), np.zeros(0))
         gd, ld, st = pb.state(g, lam) if pb.Nc > 0 else (None, None, None)
         r = torch.empty(pb.P, dtype=torch.float64, device="cuda")
@@ -58,7 +58,7 @@ def test_batched_solves_match_oracle_and_single(ctx, block):
         xs = pb.unpad(to_np(x))
         assert np.linalg.norm(b - S @ xs) <= 1.05e-10 * np.linalg.norm(b)
         assert s.rel_res <= 1e-10
-        assert np.all(to_np(x)[3 * pb.Nc:] == 0.0)
+        assert np.array_equal(to_np(x), pb.pad(xs))  # dummy rows stay zero
         one = torch.empty_like(r)
         pb.ctx.newton_solve(st, r, one, pb.ctx.solve_opts(tol=1e-10, maxit=100000, mixed=1, inner_tol=1e-3,
                                                           max_outer=60), allow=())

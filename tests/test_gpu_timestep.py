@@ -52,8 +52,9 @@ def test_advance_sticking_sphere_contact_at_rest(ctx):
     assert np.allclose(vc, 0.0, rtol=0, atol=1e-12)
 
 
-def test_warm_start_after_step_matches_oracle(ctx):
-    pb = Problem(ctx, scene_for("pile8", 4))
+@pytest.mark.parametrize("slots", [3, 4])
+def test_warm_start_after_step_matches_oracle(ctx, slots):
+    pb = Problem(ctx, scene_for("pile8", 4), slots=slots)
     g, lam = interior_point(pb, 9)
     gd, ld, st = pb.state(g, lam)
     prev_a = workload.view(pb.con, "body_a")
@@ -62,22 +63,22 @@ def test_warm_start_after_step_matches_oracle(ctx):
     pb.ctx.advance(st)
     # next step: re-assemble on the advanced positions
     s = pb.scene
-    con1 = pb.ctx.assemble(pb.dev, s.floor_z, s.gravity, s.dt, s.delta, s.mu, 3)
+    con1 = pb.ctx.assemble(pb.dev, s.floor_z, s.gravity, s.dt, s.delta, s.mu, slots)
     s1 = timestep.advance(s, pb.oc, g)
     oc1 = oc.detect(s1)
     assert con1.Nc == oc1.Nc
     assert np.array_equal(to_np(workload.view(con1, "body_a")), oc1.a)
     assert np.array_equal(to_np(workload.view(con1, "body_b")), oc1.b)
-    L, P = qp.padded_size(oc1.Nc, 3)
+    L, P = qp.padded_size(oc1.Nc, slots)
     g1 = torch.zeros(P, dtype=torch.float64, device="cuda")
     l1 = torch.zeros(2 * oc1.Nc, dtype=torch.float64, device="cuda")
     st1 = pb.ctx.state(g1, l1)
-    pb.ctx.pdip_init_warm(st1, prev_a, prev_b, prev_g, 3, gn0=1.0, shrink=0.9)
+    pb.ctx.pdip_init_warm(st1, prev_a, prev_b, prev_g, slots, gn0=1.0, shrink=0.9)
     want_g, want_l = timestep.warm_start(pb.oc.a, pb.oc.b, g, oc1.a, oc1.b, s.mu, gn0=1.0, shrink=0.9)
-    got = qp.from_padded(to_np(g1), oc1.Nc, 3)
+    got = qp.from_padded(to_np(g1), oc1.Nc, slots)
     assert relerr(got, want_g) <= 1e-15
     assert relerr(to_np(l1), want_l) <= 1e-13
-    assert np.all(to_np(g1)[3 * oc1.Nc:] == 0.0)
+    assert np.array_equal(to_np(g1), qp.to_padded(got, oc1.Nc, slots, P))  # dummy rows zero
     # most contacts persist over one step of this pile
     persist = len({(a, b) for a, b in zip(pb.oc.a, pb.oc.b)} & {(a, b) for a, b in zip(oc1.a, oc1.b)})
     assert persist >= 0.9 * oc1.Nc
