@@ -338,10 +338,14 @@ constexpr int PLAN_CON = 3;
 struct GatherPlan {
   int code[PLAN_INC][NT];
   int n[NT];                 // incidences of the thread's first body (0: none)
+  int off[NT];               // its first incidence, counted from the block's first
   int ca[PLAN_CON][NT];
   int cb[PLAN_CON][NT];
   int b0, b1;                // bodies [b0, b1) of this block
   int c0, c1;                // contacts [c0, c1) of this block
+  int base;                  // the block's first incidence (CSR position)
+  int ncache;                // incidences whose geometry is cached (0: no cache)
+  const float4* cache;       // [ncache][3] sign-folded frame and arm per incidence
 };
 
 // first body whose incidence range ends above k (bptr is nondecreasing)
@@ -367,14 +371,22 @@ __device__ void plan_fill(const SysView<T>& s, GatherPlan& pl) {
     pl.c1 = (int)(s.Nc * (g + 1) / G);
   }
   __syncthreads();
-  int n = 0;
+  if (t == 0) {
+    pl.base = s.M > 0 ? __ldg(s.bptr + pl.b0) : 0;
+    pl.ncache = 0;
+    pl.cache = nullptr;
+  }
+  __syncthreads();
+  int n = 0, off = 0;
   const int b = pl.b0 + t;
   if (b < pl.b1) {
     const int k0 = __ldg(s.bptr + b);
     n = __ldg(s.bptr + b + 1) - k0;
+    off = k0 - pl.base;
     for (int j = 0; j < PLAN_INC && j < n; ++j) pl.code[j][t] = __ldg(s.inc + k0 + j);
   }
   pl.n[t] = n;
+  pl.off[t] = off;
 #pragma unroll
   for (int k = 0; k < PLAN_CON; ++k) {
     const int c = pl.c0 + t + k * (int)blockDim.x;
@@ -382,6 +394,98 @@ __device__ void plan_fill(const SysView<T>& s, GatherPlan& pl) {
     pl.cb[k][t] = c < pl.c1 ? __ldg(s.cb + c) : 0;
   }
   __syncthreads();
+}
+
+// Cache in shared memory, for the whole launch, the geometry the body gather
+// needs from each incidence of the block's bodies (the first `cap` of them):
+// the contact frame with the side's sign folded in, and the side's arm,
+//   q[0] = s (n.x n.y n.z t1.x), q[1] = s (t1.y t1.z t2.x t2.y),
+//   q[2] = (s t2.z, arm.x, arm.y, arm.z),  s = +1 for body b, -1 for body a,
+// so that f = [q] x and the torque is arm x f.  Record loads were the largest
+// part of the gather's time.
+__device__ void plan_fill_cache(const SysView<float>& s, GatherPlan& pl, float4* cache, int cap) {
+  const int nb = pl.b1 > pl.b0 ? __ldg(s.bptr + pl.b1) - pl.base : 0;
+  const int nc = nb < cap ? nb : cap;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int code = __ldg(s.inc + pl.base + k);
+    const int c = code >> 1;
+    const bool side_b = (code & 1) != 0;
+    float R[16];
+    load_rec(s.rec, c, R);
+    const float sg = side_b ? 1.f : -1.f;
+    const float a0 = side_b ? R[12] : R[9], a1 = side_b ? R[13] : R[10], a2 = side_b ? R[14] : R[11];
+    cache[3 * k] = make_float4(sg * R[0], sg * R[1], sg * R[2], sg * R[3]);
+    cache[3 * k + 1] = make_float4(sg * R[4], sg * R[5], sg * R[6], sg * R[7]);
+    cache[3 * k + 2] = make_float4(sg * R[8], a0, a1, a2);
+  }
+  if (threadIdx.x == 0) {
+    pl.ncache = nc;
+    pl.cache = cache;
+  }
+  __syncthreads();
+}
+
+// body_gather for the thread's planned body with the cached geometry: per
+// incidence three shared-memory loads and the operand's rows.
+template <class X>
+__device__ __forceinline__ void body_gather_cached(const SysView<float>& s, const X& x, const GatherPlan& pl, int b) {
+  const int t = threadIdx.x;
+  const int n = pl.n[t], off = pl.off[t];
+  float F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
+  const float im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+  constexpr int NB = 4;
+#pragma unroll
+  for (int k0 = 0; k0 < PLAN_INC; k0 += NB) {
+    if (k0 < n) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (k0 + j < n) {
+          const int code = pl.code[k0 + j][t];
+          const int k = off + k0 + j;
+          const long long row = (long long)s.slots * (code >> 1);
+          const float x0 = x(row), x1 = x(row + 1), x2 = x(row + 2);
+          float f0, f1, f2, a0, a1, a2;
+          if (k < pl.ncache) {
+            const float4 q0 = pl.cache[3 * k], q1 = pl.cache[3 * k + 1], q2 = pl.cache[3 * k + 2];
+            f0 = q0.x * x0 + q0.w * x1 + q1.z * x2;
+            f1 = q0.y * x0 + q1.x * x1 + q1.w * x2;
+            f2 = q0.z * x0 + q1.y * x1 + q2.x * x2;
+            a0 = q2.y;
+            a1 = q2.z;
+            a2 = q2.w;
+          } else {
+            float R[16];
+            load_rec(s.rec, code >> 1, R);
+            const bool side_b = (code & 1) != 0;
+            const float sg = side_b ? 1.f : -1.f;
+            f0 = sg * (R[0] * x0 + R[3] * x1 + R[6] * x2);
+            f1 = sg * (R[1] * x0 + R[4] * x1 + R[7] * x2);
+            f2 = sg * (R[2] * x0 + R[5] * x1 + R[8] * x2);
+            a0 = side_b ? R[12] : R[9];
+            a1 = side_b ? R[13] : R[10];
+            a2 = side_b ? R[14] : R[11];
+          }
+          F0 += f0;
+          F1 += f1;
+          F2 += f2;
+          Q0 += a1 * f2 - a2 * f1;
+          Q1 += a2 * f0 - a0 * f2;
+          Q2 += a0 * f1 - a1 * f0;
+        }
+      }
+    }
+  }
+  if (n > PLAN_INC) {
+    const int b0 = __ldg(s.bptr + b);
+    for (int k0 = b0 + PLAN_INC; k0 < b0 + n; k0 += NB) {
+      int code[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) code[j] = (k0 + j < b0 + n) ? __ldg(s.inc + k0 + j) : -1;
+      gather_batch<NB>(s, x, code, F0, F1, F2, Q0, Q1, Q2);
+    }
+  }
+  float v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
+  store_w(s.w, b, v);
 }
 
 // body_gather for the thread's planned body b (= b0 + threadIdx.x).
@@ -476,6 +580,13 @@ __device__ __forceinline__ T contact_apply(const SysView<T>& s, const X& x, T* y
 template <class T, class X, int NB = gather_nb<T>()>
 __device__ __forceinline__ void gather_all(const SysView<T>& s, const X& x, const GatherPlan& pl) {
   const int b = pl.b0 + threadIdx.x;
+  if constexpr (sizeof(T) == 4) {
+    if (pl.cache) {
+      if (b < pl.b1) body_gather_cached(s, x, pl, b);
+      for (int bd = b + blockDim.x; bd < pl.b1; bd += blockDim.x) body_gather<T, X, NB>(s, x, bd);
+      return;
+    }
+  }
   if (b < pl.b1) body_gather_planned<T, X, NB>(s, x, pl, b);
   for (int bd = b + blockDim.x; bd < pl.b1; bd += blockDim.x) body_gather<T, X, NB>(s, x, bd);
 }
@@ -592,6 +703,7 @@ struct PcgArgs {
   void* xb;                 // BiCGSTAB vectors (type T), 5 * P
   int krylov;               // QP_CG or QP_BICGSTAB
   int direct;               // QTT direct mode: the inner solve is one application of X
+  int rec_cache;            // incidences of a block whose gather geometry is cached in shared memory (0: none)
   double tol, inner_tol;
   int maxit, max_outer;
   DevCtl* ctl;
@@ -969,8 +1081,12 @@ __device__ int inner_bicgstab(const PcgArgs& A, double tol, int maxit, int& iter
 template <class T, class TC>
 __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
   __shared__ GatherPlan pl;
+  extern __shared__ float4 rec_cache[];
   barrier_init();
   plan_fill(A.s64, pl);
+  if constexpr (sizeof(T) == 4) {
+    if (A.rec_cache > 0) plan_fill_cache(A.s32, pl, rec_cache, A.rec_cache);
+  }
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -2227,6 +2343,7 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   A.qw0 = A.qw1 = nullptr;
   A.krylov = o->krylov == QP_BICGSTAB ? QP_BICGSTAB : QP_CG;
   A.direct = o->precond == QP_QTT_DIRECT ? 1 : 0;
+  A.rec_cache = 0;
   A.xb = A.krylov == QP_BICGSTAB ? c->dm[12].ensure(5 * P * es) : nullptr;
   qp_dtype cdt = QP_F64;
   if (use_qtt) {
@@ -2287,7 +2404,31 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
       }
     } else if (mixed) {
       auto k = k_pcg<float, void>;
-      coop_launch(c, k, coop_grid(c, k), A);
+      // geometry cache of the body gather: as many incidences as the shared
+      // memory left by the kernel's static arrays holds (48 bytes each)
+      static int cap = -1;
+      if (cap < 0) {
+        cudaFuncAttributes fa;
+        QP_CUDA(cudaFuncGetAttributes(&fa, k));
+        int optin = 0;
+        QP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        const long long room = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
+        cap = room > 0 ? (int)std::min<long long>(room / (3 * (long long)sizeof(float4)), 4096) : 0;
+        if (cap > 0)
+          QP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       cap * 3 * (int)sizeof(float4)));
+      }
+      // only as much as a block needs (its share of the incidences), so that the
+      // rest of the unified L1 / shared memory stays L1 cache
+      const long long need = 2LL * c->Nc / c->num_sms + 64;
+      A.rec_cache = (int)std::min<long long>(cap, need);
+      const size_t smem = (size_t)A.rec_cache * 3 * sizeof(float4);
+      int per_sm = 0;
+      QP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+      QP_REQUIRE(per_sm > 0, QP_CUDA_ERROR, "cooperative kernel does not fit on an SM");
+      void* args[] = {&A};
+      QP_CUDA(cudaLaunchCooperativeKernel((const void*)k, dim3(c->num_sms * (per_sm > 2 ? 2 : per_sm)), dim3(NT),
+                                          args, smem, c->stream));
     } else if (use_qtt) {
       auto k = k_pcg<double, double>;
       coop_launch(c, k, coop_grid(c, k), A);
