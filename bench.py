@@ -159,7 +159,7 @@ def job_throughput(local_units, local_ms, world):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pcg<float, void>
 # launch of the 40^3 window, from an ncu capture of this kernel version (caches
 # flushed by ncu before the launch).  Reset to None when the kernel changes.
-KPCG_DRAM_BYTES_PER_LAUNCH = 191.34e6
+KPCG_DRAM_BYTES_PER_LAUNCH = 184.56e6
 
 
 # FP32 CUDA-core peak of the part from its unit counts: 152 SMs x 128 FP32 lanes x
