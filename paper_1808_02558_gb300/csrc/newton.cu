@@ -2406,8 +2406,10 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
       auto k = k_pcg<float, void>;
       // geometry cache of the body gather: as many incidences as the shared
       // memory left by the kernel's static arrays holds (48 bytes each)
-      static int cap = -1;
-      if (cap < 0) {
+      static int cap_of[64];  // per device; 0: not yet measured, else 1 + capacity
+      int& slot = cap_of[c->device & 63];
+      int cap = slot - 1;
+      if (slot == 0) {
         cudaFuncAttributes fa;
         QP_CUDA(cudaFuncGetAttributes(&fa, k));
         int optin = 0;
@@ -2417,6 +2419,7 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
         if (cap > 0)
           QP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        cap * 3 * (int)sizeof(float4)));
+        slot = cap + 1;
       }
       // only as much as a block needs (its share of the incidences), so that the
       // rest of the unified L1 / shared memory stays L1 cache
