@@ -25,36 +25,50 @@ struct Box {
   double lo[3], hi[3], rmax;
 };
 
-// One block: bounding box of the sphere centres and the largest radius.
-__global__ void k_body_box(int M, const double* __restrict__ pos, const double* __restrict__ rad, Box* out) {
+// Bounding box of n points (SoA [3][n]) and, when r is given, the largest r:
+// block g reduces a grid-stride share into part[g][7] = (lo xyz, hi xyz, rmax);
+// k_box_final combines the partials.  min/max are exact, so the result does
+// not depend on the split.
+constexpr int BOX_BLOCKS = 128;
+
+__global__ void k_box_partial(int n, const double* __restrict__ p, const double* __restrict__ r,
+                              double* __restrict__ part) {
   __shared__ double sm[7][32];
   double v[7] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0};
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     for (int a = 0; a < 3; ++a) {
-      double x = pos[(size_t)a * M + i];
+      const double x = p[(size_t)a * n + i];
       v[a] = fmin(v[a], x);
       v[3 + a] = fmax(v[3 + a], x);
     }
-    v[6] = fmax(v[6], rad[i]);
+    if (r) v[6] = fmax(v[6], r[i]);
   }
   for (int k = 0; k < 7; ++k) {
     double x = v[k];
     for (int o = 16; o > 0; o >>= 1) {
-      double y = __shfl_xor_sync(0xffffffffu, x, o);
+      const double y = __shfl_xor_sync(0xffffffffu, x, o);
       x = (k < 3) ? fmin(x, y) : fmax(x, y);
     }
     if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int nw = blockDim.x >> 5;
-    for (int k = 0; k < 7; ++k) {
-      double x = sm[k][0];
-      for (int w = 1; w < nw; ++w) x = (k < 3) ? fmin(x, sm[k][w]) : fmax(x, sm[k][w]);
-      if (k < 3) out->lo[k] = x;
-      else if (k < 6) out->hi[k - 3] = x;
-      else out->rmax = x;
+  if (threadIdx.x < 7) {
+    const int k = threadIdx.x, nw = blockDim.x >> 5;
+    double x = sm[k][0];
+    for (int w = 1; w < nw; ++w) x = (k < 3) ? fmin(x, sm[k][w]) : fmax(x, sm[k][w]);
+    part[(size_t)blockIdx.x * 7 + k] = x;
+  }
+}
+
+__global__ void k_box_final(int G, const double* __restrict__ part, double* __restrict__ out, int nout) {
+  const int k = threadIdx.x;
+  if (k < nout) {
+    double x = part[k];
+    for (int g = 1; g < G; ++g) {
+      const double y = part[(size_t)g * 7 + k];
+      x = (k < 3) ? fmin(x, y) : fmax(x, y);
     }
+    out[k] = x;
   }
 }
 
@@ -193,34 +207,6 @@ __global__ void k_geom_raw(int n, int M, const double* __restrict__ pos, const d
   pt[2 * (size_t)n + i] = pz;
   abkey[i] = (unsigned long long)a * (unsigned long long)(M + 1) + (unsigned long long)b;
   idx[i] = i;
-}
-
-__global__ void k_point_box(int n, const double* __restrict__ pt, double* __restrict__ box) {
-  __shared__ double sm[6][32];
-  double v[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    for (int a = 0; a < 3; ++a) {
-      double x = pt[(size_t)a * n + i];
-      v[a] = fmin(v[a], x);
-      v[3 + a] = fmax(v[3 + a], x);
-    }
-  for (int k = 0; k < 6; ++k) {
-    double x = v[k];
-    for (int o = 16; o > 0; o >>= 1) {
-      double y = __shfl_xor_sync(0xffffffffu, x, o);
-      x = (k < 3) ? fmin(x, y) : fmax(x, y);
-    }
-    if ((threadIdx.x & 31) == 0) sm[k][threadIdx.x >> 5] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int nw = blockDim.x >> 5;
-    for (int k = 0; k < 6; ++k) {
-      double x = sm[k][0];
-      for (int w = 1; w < nw; ++w) x = (k < 3) ? fmin(x, sm[k][w]) : fmax(x, sm[k][w]);
-      box[k] = x;
-    }
-  }
 }
 
 __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
@@ -401,8 +387,15 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   const int TB = 256;
 
   // 1. bounding box and uniform grid (cell >= 2 r_max + delta)
-  Box* dbox = static_cast<Box*>(c->scratch[0].ensure(sizeof(Box) + 64));
-  k_body_box<<<1, 1024, 0, st>>>(M, s->pos, s->radius, dbox);
+  // scratch[0]: body box (Box), point box (6 doubles) at +64, block partials at +256
+  char* sb = static_cast<char*>(c->scratch[0].ensure(256 + (size_t)BOX_BLOCKS * 7 * sizeof(double)));
+  Box* dbox = reinterpret_cast<Box*>(sb);
+  double* bpart = reinterpret_cast<double*>(sb + 256);
+  {
+    const int G = std::max(1, std::min(BOX_BLOCKS, ceil_div(M, 256)));
+    k_box_partial<<<G, 256, 0, st>>>(M, s->pos, s->radius, bpart);
+    k_box_final<<<1, 32, 0, st>>>(G, bpart, reinterpret_cast<double*>(dbox), 7);
+  }
   QP_CUDA(cudaGetLastError());
   Box box;
   QP_CUDA(cudaMemcpyAsync(&box, dbox, sizeof(Box), cudaMemcpyDeviceToHost, st));
@@ -528,8 +521,13 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
     cub::DeviceRadixSort::SortPairs(nullptr, t2, k2, k2s, i2, i3, Nc, 0, 3 * MORTON_BITS, st);
     tmp = c->scratch[3].ensure(tmp_bytes > t2 ? tmp_bytes : t2);
     QP_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k1, k1s, i0, i1, Nc, 0, abbits, st));
-    double* pbox = reinterpret_cast<double*>(static_cast<char*>(c->scratch[0].p) + sizeof(Box));
-    k_point_box<<<1, 1024, 0, st>>>(Nc, pt_raw, pbox);
+    double* pbox = reinterpret_cast<double*>(static_cast<char*>(c->scratch[0].p) + 64);
+    {
+      double* ppart = reinterpret_cast<double*>(static_cast<char*>(c->scratch[0].p) + 256);
+      const int G = std::max(1, std::min(BOX_BLOCKS, ceil_div(Nc, 256)));
+      k_box_partial<<<G, 256, 0, st>>>(Nc, pt_raw, nullptr, ppart);
+      k_box_final<<<1, 32, 0, st>>>(G, ppart, pbox, 6);
+    }
     k_morton<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, pt_raw, pbox, i1, k2);
     // i2 = identity positions into the (a,b)-sorted list (i0 still holds 0..Nc-1)
     QP_CUDA(cudaMemcpyAsync(i2, i0, sizeof(int) * (size_t)Nc, cudaMemcpyDeviceToDevice, st));
