@@ -113,15 +113,31 @@ __device__ __forceinline__ bool pair_active(const double* __restrict__ pos, cons
   return d2 <= dmul(s, s);
 }
 
+// FP32 copies of the centres relative to the grid origin (the FP64 difference
+// rounded once) and the radii, for the conservative pre-test of k_pairs.
+__global__ void k_pos32(int M, const double* __restrict__ pos, const double* __restrict__ rad, Grid g,
+                        float4* __restrict__ p32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x)
+    p32[i] = make_float4((float)(pos[i] - g.lo[0]), (float)(pos[(size_t)M + i] - g.lo[1]),
+                         (float)(pos[2 * (size_t)M + i] - g.lo[2]), (float)rad[i]);
+}
+
 // Count (write == nullptr) or write the contacts of body a: partners b > a in
 // the 27 neighbouring cells, then the floor.  Written pairs of one body are in
 // arbitrary order; the global order is fixed afterwards by sorting.
+// Each candidate is first tested in FP32 against an envelope widened by a bound
+// on the FP32 rounding (err: 4 x the largest coordinate error, plus a relative
+// 1e-5): only candidates that pass it take the exact FP64 test, so the pair list
+// is the exact one while most FP64 work (a narrow pipe on this part) is skipped.
 __global__ void k_pairs(int M, const double* __restrict__ pos, const double* __restrict__ rad, Grid g,
                         const int* __restrict__ cstart, const int* __restrict__ cend,
                         const int* __restrict__ sbody, double delta, double floor_z, int* __restrict__ count,
-                        const int* __restrict__ offset, int* __restrict__ wa, int* __restrict__ wb) {
+                        const int* __restrict__ offset, int* __restrict__ wa, int* __restrict__ wb,
+                        const float4* __restrict__ p32, float err) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= M) return;
+  const float4 pa = p32[a];
+  const float dl = (float)delta;
   int cx = cell_coord(pos[a], g.lo[0], g.h, g.n[0]);
   int cy = cell_coord(pos[(size_t)M + a], g.lo[1], g.h, g.n[1]);
   int cz = cell_coord(pos[2 * (size_t)M + a], g.lo[2], g.h, g.n[2]);
@@ -143,6 +159,10 @@ __global__ void k_pairs(int M, const double* __restrict__ pos, const double* __r
         for (int j = s; j < e; ++j) {
           int b = sbody[j];
           if (b <= a) continue;
+          const float4 pb = p32[b];
+          const float ex = pb.x - pa.x, ey = pb.y - pa.y, ez = pb.z - pa.z;
+          const float lim = (pa.w + pb.w + dl) + err;
+          if (ex * ex + ey * ey + ez * ez > lim * lim * 1.00001f) continue;
           if (pair_active(pos, rad, M, a, b, delta)) {
             if (wa) {
               wa[base + k] = a;
@@ -430,10 +450,19 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   k_cell_ranges<<<ceil_div(M, TB), TB, 0, st>>>(M, cell_s, cstart, cend);
 
   // 3. count, scan, write pairs
-  int* count = static_cast<int*>(c->scratch[5].ensure(sizeof(int) * (2 * (size_t)M + 2)));
+  int* count = static_cast<int*>(c->scratch[5].ensure(sizeof(int) * (2 * (size_t)M + 2) + 16 * (size_t)M + 64));
   int* offset = count + M + 1;
+  float4* p32 = reinterpret_cast<float4*>(count + ((2 * (size_t)M + 2 + 3) & ~(size_t)3));
+  // rounding bound of the FP32 pre-test: each coordinate (relative to the grid
+  // origin, at most the box extent E) is off by at most E 2^-24, and the
+  // radii and delta by a relative 2^-24; a difference is then off by at most
+  // 2 E 2^-24 per axis, the distance by sqrt(3) of that
+  double ext = 0.0;
+  for (int a2 = 0; a2 < 3; ++a2) ext = std::max(ext, box.hi[a2] - box.lo[a2]);
+  const float perr = (float)(4.0 * (ext + 2.0 * box.rmax + s->delta + 1.0) * 6.0e-8) + 1e-30f;
+  k_pos32<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, p32);
   k_pairs<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, cstart, cend, body_s, s->delta, s->floor_z,
-                                          count, nullptr, nullptr, nullptr);
+                                          count, nullptr, nullptr, nullptr, p32, perr);
   QP_CUDA(cudaGetLastError());
   tmp_bytes = 0;
   cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, count, offset, M + 1, st);
@@ -508,7 +537,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   int* bptr = c->bptr.as<int>();
   if (Nc > 0) {
     k_pairs<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, cstart, cend, body_s, s->delta, s->floor_z,
-                                            nullptr, offset, wa, wb);
+                                            nullptr, offset, wa, wb, p32, perr);
     k_geom_raw<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, M, s->pos, s->radius, s->floor_z, wa, wb, phi_raw, nrm_raw,
                                                 pt_raw, k1, i0);
     QP_CUDA(cudaGetLastError());
