@@ -61,15 +61,20 @@ __global__ void k_box_partial(int n, const double* __restrict__ p, const double*
 }
 
 __global__ void k_box_final(int G, const double* __restrict__ part, double* __restrict__ out, int nout) {
-  const int k = threadIdx.x;
-  if (k < nout) {
-    double x = part[k];
-    for (int g = 1; g < G; ++g) {
-      const double y = part[(size_t)g * 7 + k];
-      x = (k < 3) ? fmin(x, y) : fmax(x, y);
-    }
-    out[k] = x;
+  // one warp per value: each lane folds a strided share of the partials, then
+  // the warp combines the lanes
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k >= nout) return;
+  double x = k < 3 ? 1e300 : (k < 6 ? -1e300 : 0.0);
+  for (int g = lane; g < G; g += 32) {
+    const double y = part[(size_t)g * 7 + k];
+    x = (k < 3) ? fmin(x, y) : fmax(x, y);
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = (k < 3) ? fmin(x, y) : fmax(x, y);
+  }
+  if (lane == 0) out[k] = x;
 }
 
 struct Grid {
@@ -414,7 +419,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   {
     const int G = std::max(1, std::min(BOX_BLOCKS, ceil_div(M, 256)));
     k_box_partial<<<G, 256, 0, st>>>(M, s->pos, s->radius, bpart);
-    k_box_final<<<1, 32, 0, st>>>(G, bpart, reinterpret_cast<double*>(dbox), 7);
+    k_box_final<<<1, 7 * 32, 0, st>>>(G, bpart, reinterpret_cast<double*>(dbox), 7);
   }
   QP_CUDA(cudaGetLastError());
   Box box;
@@ -555,7 +560,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
       double* ppart = reinterpret_cast<double*>(static_cast<char*>(c->scratch[0].p) + 256);
       const int G = std::max(1, std::min(BOX_BLOCKS, ceil_div(Nc, 256)));
       k_box_partial<<<G, 256, 0, st>>>(Nc, pt_raw, nullptr, ppart);
-      k_box_final<<<1, 32, 0, st>>>(G, ppart, pbox, 6);
+      k_box_final<<<1, 6 * 32, 0, st>>>(G, ppart, pbox, 6);
     }
     k_morton<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, pt_raw, pbox, i1, k2);
     // i2 = identity positions into the (a,b)-sorted list (i0 still holds 0..Nc-1)
