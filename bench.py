@@ -516,7 +516,8 @@ def learned_leg(args, binding, workload):
 def batched_leg(args, binding, workload):
     """Many small scenes (sides U{4..16}, mu U[0.2, 0.8], seeded): the Newton system
     at the cold start of each, solved to 1e-8 by one launch over the scene table
-    (one thread block per scene) and, for comparison, by one newton_solve per scene."""
+    (clusters of two thread blocks: a large scene on both, small scenes one per block),
+    by the same launch with one block per scene, and by one newton_solve per scene."""
     import torch
 
     from synth import lattice_scene, splitmix64_uniform
@@ -541,7 +542,7 @@ def batched_leg(args, binding, workload):
         states.append(st)
         rhs.append(r)
         dx.append(torch.empty_like(r))
-        keep.append((g, lam, con.Nc, con.M))
+        keep.append((g, lam, con.Nc, con.M, con.P))
         nc_tot += con.Nc
         p_tot += con.P
     torch.cuda.synchronize()
@@ -564,12 +565,18 @@ def batched_leg(args, binding, workload):
     torch.cuda.synchronize()
     t_s = time.perf_counter() - t0
     tb = statistics.median(t_b)
+    # the same batch with one block per scene (no scene split over a cluster)
+    _, used1 = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=0, split=1, **kw)
+    s1, _ = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=used1, split=1, **kw)
+    plan = binding.newton_batch_plan([k[4] + k[2] for k in keep], torch.cuda.get_device_properties(0).multi_processor_count)
     # algorithmic bytes of all solves (same per-scene count as the single-scene kernel)
     nbytes = sum(solve_bytes(k[2], k[3], 3 * k[2], s.iters, s.outer) for k, s in zip(keep, stats))
     hbm, src = peaks()
     ach = nbytes / (stats[0].ms / 1e3) / 1e9
     out = {"scenes": n, "sides": "U{4..16}", "mu": "U[0.2, 0.8]", "contacts": nc_tot, "padded_unknowns": p_tot,
            "block_threads": used, "tol": 1e-8, "batched_ms": tb * 1e3, "batched_device_ms": stats[0].ms,
+           "scenes_on_two_blocks": sum(1 for _, b in plan if b == -2), "clusters": len(plan),
+           "one_block_per_scene_device_ms": s1[0].ms, "one_block_per_scene_threads": used1,
            "batched_solves_per_s": n / tb, "sequential_ms": t_s * 1e3, "sequential_solves_per_s": n / t_s,
            "speedup": t_s / tb, "max_rel_res": max(s.rel_res for s in stats),
            "not_converged": sum(1 for s in stats if s.status != binding.QP_OK),

@@ -199,26 +199,46 @@ int newton_solve(qp_ctx_t ctx, const qp_state* st, const double* rhs, double* dx
 
 /* Batched Newton solves (many independent scenes in one launch): scene i is
  * the current contact set of ctxs[i] with state st[i] (NULL: S = N), solved
- * for rhs[i] -> dx[i] (device, P_i doubles each, not aliased).  One thread
- * block per scene builds the Schur blocks and the Jacobi diagonal and runs
- * FP32 Jacobi-PCG to inner_tol inside FP64 iterative refinement to tol, with
- * block-level synchronisation only; scenes start in decreasing size.  All
- * contexts must be on one device; the launch goes to ctxs[0]'s stream after
- * the other contexts' streams, and their later work waits for it.
+ * for rhs[i] -> dx[i] (device, P_i doubles each, not aliased).  The launch is
+ * made of clusters of two thread blocks, one job per cluster: a large scene
+ * runs on both blocks (hardware cluster barriers, sums through distributed
+ * shared memory), small scenes run one per block with block-level
+ * synchronisation only (see newton_batch_plan for the grouping).  Each
+ * scene's blocks build its Schur blocks and Jacobi diagonal and run FP32
+ * Jacobi-PCG to inner_tol inside FP64 iterative refinement to tol; jobs start
+ * in decreasing cost.  All contexts must be on one device; the launch goes to
+ * ctxs[0]'s stream after the other contexts' streams, and their later work
+ * waits for it.
  * block_threads: 128, 256, 512 or 1024, or 0 to pick the fastest of 256, 512
- * and 1024 by timing this batch (the choice is kept per device and batch
- * size class).  stats[i] (may be NULL): per-scene statistics; *used (may be
- * NULL): the block size used.  Returns QP_OK when every scene converged, else
- * QP_NOT_CONVERGED or QP_BREAKDOWN (first failing scene in stats).          */
+ * and 1024 by timing this batch (the choice is kept per device, batch size
+ * class and split mode).  stats[i] (may be NULL): per-scene statistics; *used
+ * (may be NULL): the block size used.  Returns QP_OK when every scene
+ * converged, else QP_NOT_CONVERGED or QP_BREAKDOWN (first failing scene in
+ * stats); QP_INVALID_ARG for a bad block size or split mode.               */
 typedef struct {
   double tol;          /* FP64 relative residual target                      */
   int maxit;           /* inner iteration cap per scene                      */
   double inner_tol;    /* FP32 inner relative tolerance (0: 1e-3)            */
   int max_outer;       /* refinement cap (0: 50)                             */
   int block_threads;   /* see above                                          */
+  int split;           /* 0: split the scenes whose cost exceeds an even
+                          share of the SMs; 1: one block per scene; 2: every
+                          scene on two blocks                                */
 } qp_batch_opts;
 int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st, const double* const* rhs,
                          double* const* dx, const qp_batch_opts* opts, qp_solve_stats* stats, int* used);
+
+/* Host only: the cluster jobs newton_solve_batched launches for scenes with
+ * the given costs (cost_host[i] >= 0; the solver uses P_i + Nc_i) on num_sms
+ * SMs with the given split mode.  jobs_host (2n ints) receives, per job in
+ * launch order, (scene, -2) for a scene run on both blocks or (a, b) for
+ * scene a on the first block and scene b on the second (b = -1: none).
+ * Scenes are taken in decreasing cost; with split = 0 a scene runs on both
+ * blocks when its cost exceeds total / num_sms; the others are paired with
+ * their neighbour in that order.  Jobs are ordered by decreasing estimate
+ * (half the cost of a split scene, the first scene's cost for a pair), ties
+ * in the order made.  Needs no device.                                      */
+int newton_batch_plan(int n, const long long* cost_host, int num_sms, int split, int* jobs_host, int* njobs);
 
 typedef struct {
   double nu;          /* t = nu * 2Nc / eta                         (10)       */

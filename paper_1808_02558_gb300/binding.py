@@ -24,7 +24,7 @@ QP_CG, QP_BICGSTAB = 0, 1
 QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
-           "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
+           "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "newton_batch_plan", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
            "ccp_advance", "qp_selftest_barrier", "mpnn_forward", "mpnn_grad", "mpnn_adam", "mpnn_warm_start", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
@@ -50,7 +50,7 @@ class State(C.Structure):
 
 class BatchOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("block_threads", C.c_int)]
+                ("block_threads", C.c_int), ("split", C.c_int)]
 
 
 class PrevContacts(C.Structure):
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "pdip_init_warm": (i, [vp, C.POINTER(State), C.POINTER(PrevContacts), d, d]),
         "newton_solve_batched": (i, [i, C.POINTER(vp), C.POINTER(C.POINTER(State)), C.POINTER(vp), C.POINTER(vp),
                                      C.POINTER(BatchOpts), C.POINTER(SolveStats), C.POINTER(i)]),
+        "newton_batch_plan": (i, [i, C.POINTER(ll), i, i, C.POINTER(i), C.POINTER(i)]),
         "ccp_advance": (i, [vp, C.POINTER(Scene), C.POINTER(State), vp, vp, vp]),
         "qp_selftest_barrier": (i, [vp, ll, i, C.POINTER(i)]),
         "mpnn_forward": (i, [vp, vp, C.POINTER(C.c_float), vp]),
@@ -377,9 +378,11 @@ class Context:
 
 
 def newton_solve_batched(ctxs, states, rhs, dx, tol=1e-8, maxit=100000, inner_tol=1e-3, max_outer=60,
-                         block_threads=0, allow=(QP_NOT_CONVERGED, QP_BREAKDOWN)):
-    """Many scenes in one launch (one thread block per scene).  ctxs: Contexts on
-    one device; states: State or None per scene; rhs, dx: device tensors.
+                         block_threads=0, split=0, allow=(QP_NOT_CONVERGED, QP_BREAKDOWN)):
+    """Many scenes in one launch (clusters of two thread blocks: a large scene on
+    both, small scenes one per block).  ctxs: Contexts on one device; states:
+    State or None per scene; rhs, dx: device tensors; split: 0 automatic, 1 one
+    block per scene, 2 every scene on two blocks.
     Returns (per-scene SolveStats list, block size used)."""
     lib = load()
     n = len(ctxs)
@@ -387,10 +390,25 @@ def newton_solve_batched(ctxs, states, rhs, dx, tol=1e-8, maxit=100000, inner_to
     sp = (C.POINTER(State) * n)(*[C.pointer(s) if s is not None else C.POINTER(State)() for s in states])
     rp = (C.c_void_p * n)(*[_ptr(t) for t in rhs])
     dp = (C.c_void_p * n)(*[_ptr(t) for t in dx])
-    opts = BatchOpts(float(tol), int(maxit), float(inner_tol), int(max_outer), int(block_threads))
+    opts = BatchOpts(float(tol), int(maxit), float(inner_tol), int(max_outer), int(block_threads), int(split))
     stats = (SolveStats * n)()
     used = C.c_int(0)
     rc = lib.newton_solve_batched(n, ch, sp, rp, dp, C.byref(opts), stats, C.byref(used))
     if rc != QP_OK and rc not in allow:
         ctxs[0]._check(rc, "newton_solve_batched")
     return list(stats), used.value
+
+
+def newton_batch_plan(costs, num_sms, split=0):
+    """The cluster jobs of newton_solve_batched for scenes of the given costs
+    (host only): a list of (scene, -2) for a scene on both blocks or (a, b) for
+    scene a and scene b (-1: none) on the two blocks, in launch order."""
+    lib = load()
+    n = len(costs)
+    cost = (C.c_longlong * max(n, 1))(*[int(c) for c in costs])
+    jobs = (C.c_int * max(2 * n, 2))()
+    nj = C.c_int(0)
+    rc = lib.newton_batch_plan(n, cost, int(num_sms), int(split), jobs, C.byref(nj))
+    if rc != QP_OK:
+        raise QPError(rc, "newton_batch_plan: " + lib.qp_status_string(rc).decode())
+    return [(jobs[2 * j], jobs[2 * j + 1]) for j in range(nj.value)]

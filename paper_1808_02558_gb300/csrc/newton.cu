@@ -26,6 +26,8 @@
 #include "internal.cuh"
 #include "qtt_dev.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace qp {
 namespace {
 
@@ -1173,10 +1175,14 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
 }
 
 // ------------------------------------------------------------------ batched scenes
-// Many independent Newton solves in one launch: one thread block per scene runs
-// the whole solve (Schur blocks, Jacobi diagonal, FP32 inner PCG, FP64
-// refinement) with block-level synchronisation only.  Scenes are taken in
-// decreasing size, so the largest start first.
+// Many independent Newton solves in one launch.  The launch is made of clusters
+// of two thread blocks, each cluster running one job: either one large scene
+// split over both blocks (rows, contacts and bodies interleaved in slices of
+// one block's width; hardware cluster barriers between phases; sums reduced
+// through distributed shared memory) or up to two small scenes, one per block,
+// with block-level synchronisation only.  Each scene's job builds the Schur
+// blocks and the Jacobi diagonal and runs the FP32 inner PCG inside the FP64
+// refinement.  Jobs start in decreasing cost, so the longest start first.
 struct BatchScene {
   SysView<double> s64;   // H = the scene's FP64 block buffer (written here)
   SysView<float> s32;
@@ -1201,10 +1207,33 @@ struct BatchOut {
   double rel;
 };
 
+// The threads working on one scene: one block, or both blocks of the cluster.
+// T is the thread's index among them and NT their number; ph counts the sums,
+// so that consecutive sums use alternate result slots.
+struct Grp {
+  int T, NT;
+  bool split;
+  unsigned ph;
+};
+
+__device__ __forceinline__ void grp_sync(const Grp& g) {
+  if (g.split) cg::this_cluster().sync();
+  else __syncthreads();
+}
+
+// Sum over the group, identical in every thread: per-warp sums, then warp 0 of
+// each block; with two blocks both read the two block totals (rank 0 first)
+// from distributed shared memory after one cluster barrier.  The per-warp
+// partials are reused only after this call's barrier; the block totals
+// alternate between two slots, so a sum never overwrites a total that the other
+// block may still be reading.
 template <int NTB, class V, int K>
-__device__ __forceinline__ void block_sum(V (&v)[K]) {
+__device__ __forceinline__ void group_sum(V (&v)[K], Grp& g) {
   __shared__ V sm[K][NTB / 32];
+  __shared__ V tot[2][K];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int slot = g.ph & 1;
+  ++g.ph;
   for (int k = 0; k < K; ++k) {
     const V x = warp_sum(v[k]);
     if (lane == 0) sm[k][wid] = x;
@@ -1214,20 +1243,28 @@ __device__ __forceinline__ void block_sum(V (&v)[K]) {
     for (int k = 0; k < K; ++k) {
       V x = lane < NTB / 32 ? sm[k][lane] : V(0);
       x = warp_sum(x);
-      if (lane == 0) sm[k][0] = x;
+      if (lane == 0) tot[slot][k] = x;
     }
   }
-  __syncthreads();
-  for (int k = 0; k < K; ++k) v[k] = sm[k][0];
-  __syncthreads();
+  if (g.split) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    const V* t0 = cl.map_shared_rank(&tot[slot][0], 0);
+    const V* t1 = cl.map_shared_rank(&tot[slot][0], 1);
+    for (int k = 0; k < K; ++k) v[k] = t0[k] + t1[k];
+  } else {
+    __syncthreads();
+    for (int k = 0; k < K; ++k) v[k] = tot[slot][k];
+  }
 }
 
-// FP32 inner PCG of one scene on S e = b (block-local).  Returns 0 converged,
-// 1 cap, 2 breakdown.
+// FP32 inner PCG of one scene on S e = b.  Returns 0 converged, 1 cap,
+// 2 breakdown; every thread of the group takes the same branch (the sums are
+// identical).
 template <int NTB>
-__device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& iters) {
+__device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& iters, Grp& g) {
   const SysView<float>& s = S.s32;
-  const int nrow = S.nrow, t = threadIdx.x;
+  const int nrow = S.nrow, t = g.T, NT = g.NT;
   const long long P = S.P;
   float* b = S.v32;
   float* e = b + P;
@@ -1238,7 +1275,7 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
   float* q = pb + P;
   const float* dinv = S.dinv32;
   float a0[2] = {0.f, 0.f};
-  for (int i = t; i < nrow; i += NTB) {
+  for (int i = t; i < nrow; i += NT) {
     const float bi = b[i];
     e[i] = 0.f;
     r[i] = bi;
@@ -1247,7 +1284,7 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
     a0[0] += bi * bi;
     a0[1] += bi * zi;
   }
-  block_sum<NTB>(a0);
+  group_sum<NTB>(a0, g);
   const float bb = a0[0];
   float rz = a0[1];
   if (bb == 0.f) return 0;
@@ -1258,21 +1295,21 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
   for (int it = 0; it < maxit; ++it) {
     if (!(rz > 0.f)) return 2;
     const Operand<float> dir{z, it == 0 ? nullptr : pold, beta};
-    for (int bd = t; bd < s.M; bd += NTB) body_gather(s, dir, bd);
-    __syncthreads();
+    for (int bd = t; bd < s.M; bd += NT) body_gather(s, dir, bd);
+    grp_sync(g);
     float a1[1] = {0.f};
-    for (int c = t; c < s.Nc; c += NTB) a1[0] += contact_apply(s, dir, q, c, pnew);
-    block_sum<NTB>(a1);
+    for (int c = t; c < s.Nc; c += NT) a1[0] += contact_apply(s, dir, q, c, pnew);
+    group_sum<NTB>(a1, g);
     const float pq = a1[0];
     if (!(pq > 0.f)) return 2;
     const float alpha = rz / pq;
     float a2[2] = {0.f, 0.f};
     // four rows per thread and pass, every load of the pass before any store
-    for (int i0 = t; i0 < nrow; i0 += 4 * NTB) {
+    for (int i0 = t; i0 < nrow; i0 += 4 * NT) {
       float pv[4], ev[4], rv[4], qv[4], dv[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int i = i0 + j * NTB;
+        const int i = i0 + j * NT;
         const bool in = i < nrow;
         pv[j] = in ? pnew[i] : 0.f;
         ev[j] = in ? e[i] : 0.f;
@@ -1282,7 +1319,7 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int i = i0 + j * NTB;
+        const int i = i0 + j * NT;
         if (i >= nrow) break;
         e[i] = ev[j] + alpha * pv[j];
         const float ri = rv[j] - alpha * qv[j];
@@ -1293,7 +1330,7 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
         a2[1] += ri * zi;
       }
     }
-    block_sum<NTB>(a2);
+    group_sum<NTB>(a2, g);
     ++iters;
     if (a2[0] <= stop) return 0;
     beta = a2[1] / rz;
@@ -1305,16 +1342,26 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
   return 1;
 }
 
+// One job per cluster: jobs[j] = (scene, -2) runs that scene on both blocks;
+// (a, b) runs scene a on block rank 0 and scene b (b >= 0) on rank 1.
 template <int NTB>
-__global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restrict__ tab, const int* __restrict__ order,
-                                                     double tol, double inner_tol, int maxit, int max_outer,
-                                                     BatchOut* __restrict__ out) {
-  const int sid = order[blockIdx.x];
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTB)
+    k_pcg_batched(const BatchScene* __restrict__ tab, const int2* __restrict__ jobs, double tol, double inner_tol,
+                  int maxit, int max_outer, BatchOut* __restrict__ out) {
+  const int rank = (int)cg::this_cluster().block_rank();
+  const int2 job = jobs[blockIdx.x >> 1];
+  Grp g;
+  g.split = job.y == -2;
+  g.ph = 0;
+  const int sid = g.split ? job.x : (rank == 0 ? job.x : job.y);
+  if (sid < 0) return;  // the second block of a job with one small scene
+  g.T = g.split ? rank * NTB + (int)threadIdx.x : (int)threadIdx.x;
+  g.NT = g.split ? 2 * NTB : NTB;
   const BatchScene S = tab[sid];
-  const int t = threadIdx.x;
+  const int t = g.T, NT = g.NT;
   const int n = S.s64.Nc;
   // Schur blocks (zero without a state) and the Jacobi diagonal
-  for (int c = t; c < n; c += NTB) {
+  for (int c = t; c < n; c += NT) {
     double h[6] = {0, 0, 0, 0, 0, 0};
     if (S.gamma) {
       const long long row = (long long)S.s64.slots * c;
@@ -1325,8 +1372,8 @@ __global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restric
       S.H32[(size_t)k * n + c] = (float)h[k];
     }
   }
-  __syncthreads();
-  for (long long i = t; i < S.P; i += NTB) {
+  grp_sync(g);
+  for (long long i = t; i < S.P; i += NT) {
     const long long c = i / S.s64.slots;
     const int u = (int)(i - c * S.s64.slots);
     double v = 1.0;
@@ -1336,8 +1383,8 @@ __global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restric
     S.dx[i] = 0.0;
   }
   double bn[1] = {0.0};
-  for (int i = t; i < S.nrow; i += NTB) bn[0] += S.rhs[i] * S.rhs[i];
-  block_sum<NTB>(bn);
+  for (int i = t; i < S.nrow; i += NT) bn[0] += S.rhs[i] * S.rhs[i];
+  group_sum<NTB>(bn, g);
   const double bnorm = sqrt(bn[0]);
   int iters = 0, outer = 0, status = 0;
   double rel = 0.0;
@@ -1345,22 +1392,22 @@ __global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restric
     for (outer = 0;; ++outer) {
       double rr[1] = {0.0};
       if (outer == 0) {
-        for (int i = t; i < S.nrow; i += NTB) {
+        for (int i = t; i < S.nrow; i += NT) {
           S.r64[i] = S.rhs[i];
           rr[0] += S.rhs[i] * S.rhs[i];
         }
       } else {
-        for (int bd = t; bd < S.s64.M; bd += NTB) body_gather(S.s64, plain<double>(S.dx), bd);
-        __syncthreads();
-        for (int c = t; c < n; c += NTB) contact_apply(S.s64, plain<double>(S.dx), S.q64, c);
-        __syncthreads();
-        for (int i = t; i < S.nrow; i += NTB) {
+        for (int bd = t; bd < S.s64.M; bd += NT) body_gather(S.s64, plain<double>(S.dx), bd);
+        grp_sync(g);
+        for (int c = t; c < n; c += NT) contact_apply(S.s64, plain<double>(S.dx), S.q64, c);
+        grp_sync(g);
+        for (int i = t; i < S.nrow; i += NT) {
           const double ri = S.rhs[i] - S.q64[i];
           S.r64[i] = ri;
           rr[0] += ri * ri;
         }
       }
-      block_sum<NTB>(rr);
+      group_sum<NTB>(rr, g);
       const double rn = sqrt(rr[0]);
       rel = rn / bnorm;
       if (rel <= tol) break;
@@ -1369,13 +1416,13 @@ __global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restric
         break;
       }
       const double inv = 1.0 / rn;
-      for (int i = t; i < S.nrow; i += NTB) S.v32[i] = (float)(S.r64[i] * inv);
-      __syncthreads();
+      for (int i = t; i < S.nrow; i += NT) S.v32[i] = (float)(S.r64[i] * inv);
+      grp_sync(g);
       const int before = iters;
-      const int st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters);
+      const int st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters, g);
       const float* e = S.v32 + S.P;
-      for (int i = t; i < S.nrow; i += NTB) S.dx[i] += rn * (double)e[i];
-      __syncthreads();
+      for (int i = t; i < S.nrow; i += NT) S.dx[i] += rn * (double)e[i];
+      grp_sync(g);
       if (st == 2 && iters == before) {
         status = 2;
         break;
@@ -1388,6 +1435,8 @@ __global__ void __launch_bounds__(NTB) k_pcg_batched(const BatchScene* __restric
     out[sid].status = status;
     out[sid].rel = rel;
   }
+  // a block's shared memory must outlive the other block's last read of it
+  if (g.split) cg::this_cluster().sync();
 }
 
 // ------------------------------------------------------------------ fused pipelined PCG
@@ -2476,24 +2525,56 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
   return st;
 }
 
-// Batched solve: build the scene table, order scenes by size, launch one
-// block per scene (block size given or measured), read the per-scene results.
-struct BatchRun {
-  std::vector<BatchScene> tab;
-  std::vector<int> order;
-};
-
-static void launch_batched(qp_ctx* c0, int nt, int n, const BatchScene* tab, const int* order, const qp_batch_opts* o,
-                           BatchOut* out) {
+// Batched solve: build the scene table, group the scenes into cluster jobs
+// (large scenes split over two blocks, small ones paired), launch one cluster
+// per job (block size given or measured), read the per-scene results.
+static void launch_batched(qp_ctx* c0, int nt, int njobs, const BatchScene* tab, const int2* jobs,
+                           const qp_batch_opts* o, BatchOut* out) {
   const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-3;
   const int mo = o->max_outer > 0 ? o->max_outer : 50;
+  const int grid = 2 * njobs;
   switch (nt) {
-    case 128: k_pcg_batched<128><<<n, 128, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
-    case 256: k_pcg_batched<256><<<n, 256, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
-    case 512: k_pcg_batched<512><<<n, 512, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
-    default: k_pcg_batched<1024><<<n, 1024, 0, c0->stream>>>(tab, order, o->tol, itol, o->maxit, mo, out); break;
+    case 128: k_pcg_batched<128><<<grid, 128, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
+    case 256: k_pcg_batched<256><<<grid, 256, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
+    case 512: k_pcg_batched<512><<<grid, 512, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
+    default: k_pcg_batched<1024><<<grid, 1024, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
   }
   QP_CUDA(cudaGetLastError());
+}
+
+// Cluster jobs from per-scene costs: with split = 0 a scene whose cost exceeds
+// an even share of the SMs (total / SM count) runs on both blocks of a
+// cluster, split = 2 splits every scene, split = 1 none.  The remaining scenes
+// are paired in decreasing cost (neighbours, so the two blocks of a cluster
+// finish together).  Jobs are ordered by decreasing time estimate: half the
+// cost for a split scene, the larger cost for a pair.
+static std::vector<int2> batch_jobs(const std::vector<long long>& cost, int num_sms, int split) {
+  const int n = (int)cost.size();
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  long long total = 0;
+  for (long long w : cost) total += w;
+  const double share = (double)total / (num_sms > 0 ? num_sms : 1);
+  std::vector<std::pair<double, int2>> jobs;
+  int pending = -1;
+  for (int i : ord) {
+    const bool big = split == 2 || (split == 0 && (double)cost[i] > share);
+    if (big) {
+      jobs.push_back({0.5 * (double)cost[i], make_int2(i, -2)});
+    } else if (pending < 0) {
+      pending = i;
+    } else {
+      jobs.push_back({(double)cost[pending], make_int2(pending, i)});
+      pending = -1;
+    }
+  }
+  if (pending >= 0) jobs.push_back({(double)cost[pending], make_int2(pending, -1)});
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [](const std::pair<double, int2>& a, const std::pair<double, int2>& b) { return a.first > b.first; });
+  std::vector<int2> out(jobs.size());
+  for (size_t j = 0; j < jobs.size(); ++j) out[j] = jobs[j].second;
+  return out;
 }
 
 // measured block size per (device, batch size class)
@@ -2504,7 +2585,7 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
                          double* const* dx, const qp_batch_opts* o, qp_solve_stats* stats, int* used) {
   qp_ctx* c0 = ctxs[0];
   std::vector<BatchScene> tab(n);
-  std::vector<std::pair<long long, int>> bysize(n);
+  std::vector<long long> cost(n);
   long long work = 0;
   for (int i = 0; i < n; ++i) {
     qp_ctx* c = ctxs[i];
@@ -2532,17 +2613,17 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
     b.v32 = static_cast<float*>(c->batch32.ensure(7 * P * sizeof(float)));
     b.P = c->P;
     b.nrow = c->slots * c->Nc;
-    bysize[i] = {-(long long)c->P - c->Nc, i};
+    cost[i] = (long long)c->P + c->Nc;
     work += c->P;
   }
-  std::sort(bysize.begin(), bysize.end());
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = bysize[i].second;
-  // table, order and outputs in one device buffer of ctxs[0]
-  const size_t tb = sizeof(BatchScene) * n, ob = sizeof(int) * n, rb = sizeof(BatchOut) * n;
+  QP_REQUIRE(o->split >= 0 && o->split <= 2, QP_INVALID_ARG, "newton_solve_batched: split must be 0, 1 or 2");
+  const std::vector<int2> jobs = batch_jobs(cost, c0->num_sms, o->split);
+  const int nj = (int)jobs.size();
+  // table, jobs and outputs in one device buffer of ctxs[0]
+  const size_t tb = sizeof(BatchScene) * n, ob = sizeof(int2) * n, rb = sizeof(BatchOut) * n;
   char* buf = static_cast<char*>(c0->batch_table.ensure(tb + 256 + ob + 256 + rb));
   BatchScene* dtab = reinterpret_cast<BatchScene*>(buf);
-  int* dorder = reinterpret_cast<int*>(buf + ((tb + 255) / 256) * 256);
+  int2* djobs = reinterpret_cast<int2*>(buf + ((tb + 255) / 256) * 256);
   BatchOut* dout = reinterpret_cast<BatchOut*>(buf + ((tb + 255) / 256) * 256 + ((ob + 255) / 256) * 256);
   // the other contexts' pending work (assembly, states) comes first
   for (int i = 0; i < n; ++i)
@@ -2551,14 +2632,14 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
       QP_CUDA(cudaStreamWaitEvent(c0->stream, ctxs[i]->ev0, 0));
     }
   QP_CUDA(cudaMemcpyAsync(dtab, tab.data(), tb, cudaMemcpyHostToDevice, c0->stream));
-  QP_CUDA(cudaMemcpyAsync(dorder, order.data(), ob, cudaMemcpyHostToDevice, c0->stream));
+  QP_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(int2) * nj, cudaMemcpyHostToDevice, c0->stream));
   int nt = o->block_threads;
   QP_REQUIRE(nt == 0 || nt == 128 || nt == 256 || nt == 512 || nt == 1024, QP_INVALID_ARG,
              "newton_solve_batched: block_threads must be 0, 128, 256, 512 or 1024");
   if (nt == 0) {
     long long cls = 1;
     while (cls < work / n) cls <<= 1;
-    const auto key = std::make_pair(c0->device, cls * 4096 + (n < 4096 ? n / 64 : 64));
+    const auto key = std::make_pair(c0->device, (cls * 4096 + (n < 4096 ? n / 64 : 64)) * 4 + o->split);
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune.find(key);
@@ -2568,7 +2649,7 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
       float best = 1e30f;
       for (int cand : {256, 512, 1024}) {
         QP_CUDA(cudaEventRecord(c0->ev0, c0->stream));
-        launch_batched(c0, cand, n, dtab, dorder, o, dout);
+        launch_batched(c0, cand, nj, dtab, djobs, o, dout);
         QP_CUDA(cudaEventRecord(c0->ev1, c0->stream));
         QP_CUDA(cudaEventSynchronize(c0->ev1));
         float ms = 0;
@@ -2583,7 +2664,7 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
     }
   }
   QP_CUDA(cudaEventRecord(c0->ev0, c0->stream));
-  launch_batched(c0, nt, n, dtab, dorder, o, dout);
+  launch_batched(c0, nt, nj, dtab, djobs, o, dout);
   QP_CUDA(cudaEventRecord(c0->ev1, c0->stream));
   std::vector<BatchOut> res(n);
   QP_CUDA(cudaMemcpyAsync(res.data(), dout, rb, cudaMemcpyDeviceToHost, c0->stream));
@@ -2693,6 +2774,19 @@ int newton_solve(qp_ctx_t c, const qp_state* st, const double* rhs, double* dx, 
   if (s.status == QP_TIMEOUT) throw Error{QP_TIMEOUT, "newton_solve: device barrier wait expired"};
   return s.status;
   API_END(c)
+}
+
+int newton_batch_plan(int n, const long long* cost_host, int num_sms, int split, int* jobs_host, int* njobs) {
+  if (n < 0 || (n > 0 && (!cost_host || !jobs_host)) || !njobs || split < 0 || split > 2) return QP_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (cost_host[i] < 0) return QP_INVALID_ARG;
+  const std::vector<int2> jobs = batch_jobs(std::vector<long long>(cost_host, cost_host + n), num_sms, split);
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    jobs_host[2 * j] = jobs[j].x;
+    jobs_host[2 * j + 1] = jobs[j].y;
+  }
+  *njobs = (int)jobs.size();
+  return QP_OK;
 }
 
 int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st, const double* const* rhs,

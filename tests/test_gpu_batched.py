@@ -28,10 +28,17 @@ def scenes():
     return out
 
 
-@pytest.mark.parametrize("block,slots", [(256, 3), (0, 3), (512, 4)])
-def test_batched_solves_match_oracle_and_single(ctx, block, slots):
+@pytest.mark.parametrize("block,slots,split", [(256, 3, 0), (0, 3, 0), (512, 4, 0), (1024, 3, 1), (256, 4, 2),
+                                               (128, 3, 1)])
+def test_batched_solves_match_oracle_and_single(ctx, block, slots, split):
+    """split 0: the scenes above an even share of the SMs run on two blocks;
+    1: one block per scene (scenes paired in clusters); 2: every scene on two
+    blocks."""
     pbs, states, rhs, dx, keep = [], [], [], [], []
-    for i, s in enumerate(scenes()):
+    sc = scenes()
+    if block == 128:  # an odd count leaves the second block of the last cluster idle
+        sc = sc[:3]
+    for i, s in enumerate(sc):
         pb = Problem(ctx, s, slots=slots)
         g, lam = interior_point(pb, i) if pb.Nc > 0 else (np.zeros(0), np.zeros(0))
         gd, ld, st = pb.state(g, lam) if pb.Nc > 0 else (None, None, None)
@@ -46,8 +53,8 @@ def test_batched_solves_match_oracle_and_single(ctx, block, slots):
         dx.append(torch.full_like(r, 9.0))
         keep.append((gd, ld))
     stats, used = binding.newton_solve_batched([p[0].ctx for p in pbs], states, rhs, dx, tol=1e-10,
-                                               block_threads=block, allow=())
-    assert used in (256, 512, 1024)
+                                               block_threads=block, split=split, allow=())
+    assert used == block if block else used in (256, 512, 1024)
     for (pb, g, lam), st, r, x, s in zip(pbs, states, rhs, dx, stats):
         assert s.status == binding.QP_OK
         if pb.Nc == 0:
@@ -87,3 +94,30 @@ def test_batched_rejects_bad_arguments(ctx):
     with pytest.raises(binding.QPError) as e:
         binding.newton_solve_batched([pb.ctx], [None], [b], [x], tol=1e-8, block_threads=100, allow=())
     assert e.value.code == binding.QP_INVALID_ARG
+    with pytest.raises(binding.QPError) as e:
+        binding.newton_solve_batched([pb.ctx], [None], [b], [x], tol=1e-8, split=3, allow=())
+    assert e.value.code == binding.QP_INVALID_ARG
+
+
+def test_split_and_unsplit_solves_agree(ctx):
+    """The same 20^3 Newton system on one block and on a two-block cluster: both
+    reach the tolerance and agree to it (the sums are taken in a different
+    order, so not bitwise)."""
+    s = lattice_scene(20, 5)
+    pb = Problem(ctx, s)
+    g, lam = interior_point(pb, 3)
+    gd, ld, st = pb.state(g, lam)
+    r = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+    pb.ctx.newton_rhs(st, r)
+    out = {}
+    for split in (1, 2):
+        x = torch.full_like(r, 9.0)
+        stats, _ = binding.newton_solve_batched([pb.ctx], [st], [r], [x], tol=1e-10, block_threads=512,
+                                                split=split, allow=())
+        assert stats[0].status == binding.QP_OK and stats[0].rel_res <= 1e-10
+        out[split] = pb.unpad(to_np(x))
+    S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+    b = pb.unpad(to_np(r))
+    for x in out.values():
+        assert np.linalg.norm(b - S @ x) <= 1.05e-10 * np.linalg.norm(b)
+    assert relerr(out[2], out[1]) <= 1e-8
