@@ -1,5 +1,6 @@
-"""GPU parity: many independent Newton systems in one launch (one thread block
-per scene) against the oracle's Schur matrices and the single-scene solver."""
+"""GPU parity: many independent Newton systems in one launch (two-block
+clusters: a scene on both blocks or one scene per block) against the oracle's
+Schur matrices and the single-scene solver."""
 import numpy as np
 import pytest
 import torch
