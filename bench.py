@@ -393,6 +393,7 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_ms_max = max_over_ranks(statistics.median(e2e_ms), world)
 
+    apply_out = n_apply_leg(binding, ctx, st, Nc, M, P, flush, stream, args.apply_reps) if args.apply_reps > 0 else None
     ts_out = time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream) if args.ts_steps > 0 else None
     batch_out = batched_leg(args, binding, workload) if args.batch_scenes > 0 else None
     learned_out = learned_leg(args, binding, workload) if args.learned_steps > 0 else None
@@ -415,6 +416,7 @@ def run_ours(args):
                      "traffic": KPCG_DRAM_BYTES_PER_LAUNCH if args.workload == "pile40p" else None,
                      "traffic_unit": "bytes per launch (one Newton solve)"},
         "qtt_pcg": qtt_out,
+        "n_apply": apply_out,
         "e2e": {"value": args.window * 1e3 / e2e_ms_max * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
@@ -434,6 +436,63 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (nominal; no measured figure)
+
+
+def n_apply_leg(binding, ctx, st, Nc, M, P, flush, stream, reps=20):
+    """The standalone operator apply y = S x (newton_apply) on the bench's scene,
+    FP64 and FP32, with and without the PDIP blocks, L2 flushed before every
+    timed call.  Algorithmic bytes, FP64 (FP32 halves the values): per contact
+    x 24 + y 24 + frame (n, t1) 48 + arms 48 + ids 8 = 152 B, plus, with the
+    state, gamma 24 + lambda 16 read and H 48 written and read (136 B); per body
+    1/m, 1/I 16 + w written 48 + read 48 = 112 B.  Pad rows are excluded.
+    Flops: 33 per incidence (two per contact), 47 per contact in the contact pass
+    (65 with H), 6 per body, and 27 per contact for the Schur blocks.  The bound
+    is HBM when flop/byte is below the ridge of the dtype's ALU peak over the
+    measured HBM peak (FP32: 80.5 TFLOP/s derived; FP64: 1.25 TFLOP/s nominal),
+    else that ALU peak."""
+    import torch
+
+    hbm, src = peaks()
+    out = {}
+    for name, dt, vb in (("f64", binding.QP_F64, 8), ("f32", binding.QP_F32, 4)):
+        tdt = torch.float64 if vb == 8 else torch.float32
+        alu = FP64_TFLOPS_NOMINAL if vb == 8 else FP32_ALU_TFLOPS
+        alu_src = "nominal" if vb == 8 else "derived: 152 SM x 128 FP32 x 2 x 2.07 GHz"
+        x = torch.randn(P, dtype=tdt, device="cuda")
+        y = torch.empty_like(x)
+        for with_state in (False, True):
+            s_ = st if with_state else None
+            for _ in range(3):
+                ctx.newton_apply(s_, x, y, dt)
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.newton_apply(s_, x, y, dt)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            per_c = 18 * vb + 8 + ((5 + 12) * vb if with_state else 0)
+            nbytes = Nc * per_c + M * 14 * vb
+            flops = Nc * (2 * 33 + (65 + 27 if with_state else 47)) + M * 6
+            t = statistics.median(ms) / 1e3
+            if flops / nbytes < alu * 1e12 / (hbm * 1e9):
+                roof = {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": nbytes / t / 1e9 / hbm, "peak_source": src}
+            else:
+                roof = {"bound": "alu", "achieved": flops / t / 1e12, "peak": alu, "unit": "TFLOP/s",
+                        "frac": flops / t / 1e12 / alu, "peak_source": alu_src}
+            key = name + ("_with_state" if with_state else "")
+            out[key] = {"us": t * 1e6, "bytes": nbytes, "flops": flops, "launches": 3 if with_state else 2,
+                        "gbs": nbytes / t / 1e9, "roofline": roof}
+    out["note"] = ("median of %d calls, L2 flushed before each; with_state includes the Schur-block "
+                   "build from (gamma, lambda)" % reps)
+    return out
 
 
 def learned_leg(args, binding, workload):
@@ -763,6 +822,7 @@ def main():
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "qtt"])
     ap.add_argument("--workload", default="pile40p", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-reps", type=int, default=20, help="timed newton_apply calls per variant (0: skip)")
     ap.add_argument("--qtt-eps", type=float, default=1e-2)
     ap.add_argument("--qtt-rmax", type=int, default=10)
     ap.add_argument("--qtt-steps", type=int, default=1, help="PDIP steps of the QTT-PCG comparison leg (0: skip)")

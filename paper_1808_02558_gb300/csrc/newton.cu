@@ -610,9 +610,44 @@ __device__ __forceinline__ Operand<T> plain(const T* x) {
   return Operand<T>{x, nullptr, T(0)};
 }
 
-template <class T>
-__global__ void k_body_gather(SysView<T> s, const T* x) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < s.M; b += gridDim.x * blockDim.x) body_gather(s, plain(x), b);
+// Standalone body gather with L lanes per body, one body per lane group (no
+// grid-stride loop, so every lane reaches the shuffles): lane j takes the
+// body's incidences j, j + L, ... two at a time, the L partial force and
+// torque sums are combined by butterfly shuffles within the aligned group, and
+// lane 0 scales and stores w_b.  A thread per body leaves too few loads in
+// flight when the caches are cold (64 k bodies on 152 SMs); four lanes per body
+// measured faster than one or eight on the 40^3 pile (FP32 apply 27 -> 23 us).
+#ifndef QP_APPLY_LANES
+#define QP_APPLY_LANES 4
+#endif
+template <class T, int L>
+__global__ void k_body_gather_lanes(SysView<T> s, const T* x) {
+  static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "lanes: a power of two up to 32");
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long b = t / L;
+  const int lane = (int)(t & (L - 1));
+  T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
+  if (b < s.M) {
+    const int e = __ldg(s.bptr + b + 1);
+    for (int k = __ldg(s.bptr + b) + lane; k < e; k += 2 * L) {
+      const int code[2] = {__ldg(s.inc + k), k + L < e ? __ldg(s.inc + k + L) : -1};
+      gather_batch<2>(s, plain(x), code, F0, F1, F2, Q0, Q1, Q2);
+    }
+  }
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) {
+    F0 += __shfl_xor_sync(0xffffffffu, F0, o);
+    F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+    F2 += __shfl_xor_sync(0xffffffffu, F2, o);
+    Q0 += __shfl_xor_sync(0xffffffffu, Q0, o);
+    Q1 += __shfl_xor_sync(0xffffffffu, Q1, o);
+    Q2 += __shfl_xor_sync(0xffffffffu, Q2, o);
+  }
+  if (b < s.M && lane == 0) {
+    const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+    T v[6] = {im * F0, im * F1, im * F2, iI * Q0, iI * Q1, iI * Q2};
+    store_w(s.w, b, v);
+  }
 }
 
 template <class T>
@@ -2208,7 +2243,8 @@ void launch_rowscale(qp_ctx* c, double* rowscale) {
 void launch_apply64(qp_ctx* c, const double* x, double* y, bool with_H) {
   SysView<double> s = view64(c, with_H);
   int g = c->num_sms * 8;
-  if (c->M > 0) k_body_gather<double><<<g, 256, 0, c->stream>>>(s, x);
+  if (c->M > 0)
+    k_body_gather_lanes<double, QP_APPLY_LANES><<<ceil_div((long long)c->M * QP_APPLY_LANES, 256), 256, 0, c->stream>>>(s, x);
   k_contact_apply<double><<<g, 256, 0, c->stream>>>(s, x, y);
   QP_CUDA(cudaGetLastError());
 }
@@ -2216,7 +2252,8 @@ void launch_apply64(qp_ctx* c, const double* x, double* y, bool with_H) {
 void launch_apply32(qp_ctx* c, const float* x, float* y, bool with_H) {
   SysView<float> s = view32(c, with_H);
   int g = c->num_sms * 8;
-  if (c->M > 0) k_body_gather<float><<<g, 256, 0, c->stream>>>(s, x);
+  if (c->M > 0)
+    k_body_gather_lanes<float, QP_APPLY_LANES><<<ceil_div((long long)c->M * QP_APPLY_LANES, 256), 256, 0, c->stream>>>(s, x);
   k_contact_apply<float><<<g, 256, 0, c->stream>>>(s, x, y);
   QP_CUDA(cudaGetLastError());
 }
