@@ -428,6 +428,9 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         ctx.pdip_init(st, 1.0)
         out["cpu_baseline"] = cpu_baseline(scene, gamma, lam, statistics.mean(iters) + statistics.mean(outer))
+        if args.cpu_all_cores:
+            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload, gamma, lam,
+                                                                   out["cpu_baseline"]["iterations_per_solve"])
     ctx2.close()
     ctx.close()
     if rank == 0:
@@ -770,11 +773,65 @@ def cpu_baseline(scene, gamma=None, lam=None, iters_per_solve=None):
     info, el = oracle_sample(S, rhs)
     per_it = el / max(1, info["iters"])
     need = info["iters"] if info["converged"] else (iters_per_solve or info["iters"])
-    return {"value": 1.0 / (per_it * need), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / (per_it * need), "unit": UNIT, "cores": 1, "kind": "oracle", "iterations_per_solve": need,
             "sample": (f"oracle FP64 Jacobi-PCG (numpy/scipy, 1 thread) on the same Newton system: {info['iters']} "
                        f"iterations in {el:.1f} s ({'converged' if info['converged'] else 'capped'}); solves/s = "
                        f"1/(s per iteration x {need:.0f} iterations per solve"
                        f"{'' if info['converged'] else ', the GPU count'})")}
+
+
+def _oracle_worker(job):
+    """One host core of the all-cores CPU baseline: build the oracle's Newton
+    system, then run its Jacobi-PCG solve to 1e-8 repeatedly for `seconds`.
+    Returns (iterations, elapsed seconds of the solving window)."""
+    workload, seed, gamma_c, lam, seconds = job
+    from oracle import krylov
+    from synth import scene_for
+
+    S, rhs = oracle_system(scene_for(workload, seed=seed), gamma_c, lam)
+    its, t0 = 0, time.perf_counter()
+    while True:
+        _, info = krylov.jacobi_pcg(S, rhs, tol=1e-8, maxit=20000)
+        its += info["iters"]
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return its, el
+
+
+def cpu_baseline_all_cores(workload, gamma, lam, iters_per_solve, seconds=5.0):
+    """The oracle on every host core: one process per core (spawned, one thread
+    each), each solving the same Newton system repeatedly; the job's rate is the
+    sum of the per-core iteration rates over the iterations of one solve."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from oracle import qp
+
+    Nc = lam.numel() // 2
+    g_c = qp.from_padded(gamma.cpu().numpy(), Nc, 3)
+    l_c = lam.cpu().numpy()
+    cores = os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        # a worker that dies breaks the executor (an error, not a hang)
+        with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_oracle_worker, [(workload, 1, g_c, l_c, seconds)] * cores))
+    except Exception as e:  # reported in the line instead of failing the bench
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": repr(e)[:200]}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rate = sum(i / e for i, e in res)
+    return {"value": rate / iters_per_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle FP64 Jacobi-PCG (numpy/scipy), {cores} spawned processes of one thread, each "
+                       f"solving the same Newton system to 1e-8 repeatedly for {seconds:.0f} s "
+                       f"({sum(i for i, _ in res)} iterations in all); solves/s = sum of per-process "
+                       f"iterations/s / {iters_per_solve:.0f} iterations per solve")}
 
 
 def run_reference(args):
@@ -822,6 +879,7 @@ def main():
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "qtt"])
     ap.add_argument("--workload", default="pile40p", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", type=int, default=1, help="also time the oracle on every host core (0: skip)")
     ap.add_argument("--apply-reps", type=int, default=20, help="timed newton_apply calls per variant (0: skip)")
     ap.add_argument("--qtt-eps", type=float, default=1e-2)
     ap.add_argument("--qtt-rmax", type=int, default=10)
