@@ -31,8 +31,10 @@ void launch_step(qp_ctx* c, const QttDev& q, int k, const void* in, void* out, i
   const TV* i = static_cast<const TV*>(in);
   TV* o = static_cast<TV*>(out);
   if (bound) {
+    // one wave of the two resident blocks per SM: each block stages its two cores
+    // once and its threads stride over several column items
     long long want = ((N >> 2) + 255) / 256;
-    if (want > (long long)c->num_sms * 16) want = (long long)c->num_sms * 16;
+    if (want > (long long)c->num_sms * 2) want = (long long)c->num_sms * 2;
     k_qtt_step2<TV, TA, TC><<<(int)(want < 1 ? 1 : want), 256, 0, c->stream>>>(q, k, i, o, bound);
   } else {
     const long long items = N >> 1;
