@@ -25,7 +25,8 @@ gn_min, |gamma_t| <= shrink mu gamma_n), lambda = -1/f (centred at t = 1).
 
 Pins: the backward pass against central finite differences of the loss;
 permutation equivariance (relabelled contacts give permuted outputs); the
-warm start lies strictly inside the cones.
+message as a hand-computed body sum; the features of a sphere on a plane in
+closed form; the warm start lies strictly inside the cones.
 """
 from __future__ import annotations
 

@@ -61,3 +61,28 @@ def test_warm_start_inside_cones():
     g, lam = mpnn.warm_start(o, 2.0, 0.4, 1e-3)
     f = qp.constraints(g, 0.4)
     assert np.all(f < 0) and np.all(g[0::3] >= 1e-3) and np.all(lam > 0)
+
+
+def test_features_of_a_sphere_on_a_plane():
+    """Closed form: the floor contact's normal is +z; its frame is t1 = +y, t2 = -x
+    (n x e_x normalised, then n x t1); the relative velocity in that frame is the
+    sphere's velocity after gravity's step plus w x rho, projected; Phi/dt and mu
+    follow; each feature is multiplied by its scale."""
+    import sys
+    import os
+
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_qp import sphere_on_plane
+
+    v = np.array([0.3, -0.2, 0.05])
+    w = np.array([1.0, 2.0, -3.0])
+    s = sphere_on_plane(v, w, phi=0.01, mu=0.7)
+    con = oc.detect(s)
+    _, _, r = qp.qp_data(s, con)
+    scale = np.array([1.0, 2.0, 3.0, 0.5, 0.25, 4.0, 5.0, 6.0])
+    x = mpnn.features(s, con, r, scale)
+    rho = np.array([0.0, 0.0, -0.5 - 0.005])  # contact point (x, y, Phi/2) minus the centre
+    vel = v + s.dt * np.array(s.gravity) + np.cross(w, rho)
+    want = np.array([0.0, 0.0, 1.0, 0.01 / s.dt, vel[2], vel[1], -vel[0], 0.7]) * scale
+    assert x.shape == (1, 8)
+    assert np.allclose(x[0], want, rtol=1e-12, atol=1e-12)
