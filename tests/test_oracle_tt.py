@@ -4,6 +4,8 @@ Exact ranks of matrices whose QTT structure is known in closed form, the
 worked sin(x+y+z) example of Sec. 3.1, the TT-SVD error bound, and dense
 reconstruction of the mat-vec.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -42,14 +44,26 @@ def test_identity_padding_adds_at_most_one_rank():
     assert all(p <= b + 1 for p, b in zip(padded, base))
 
 
-def test_sine_cube_example():
-    # Sec. 3.1: sin(x+y+z) on an n^3 grid has TT ranks (2, 2) and storage 8n... (2n + 4n + 2n)
-    n = 17
+def golden(name):
+    """key -> list of ints from a fixture under tests/golden (comments start with #)."""
+    out = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if line:
+                out[line[0]] = [int(v) for v in line[1:]]
+    return out
+
+
+@pytest.mark.parametrize("n", [5, 17])
+def test_sine_cube_example(n):
+    # Sec. 3.1 worked example: ranks and storage as the paper prints them
+    g = golden("sine_cube_sec3_1.txt")
     x = np.linspace(0, 1, n)
     A = np.sin(x[:, None, None] + x[None, :, None] + x[None, None, :])
     cores = tt.tt_svd(A, 1e-12)
-    assert tt.tt_ranks(cores) == [1, 2, 2, 1]
-    assert sum(G.size for G in cores) == 8 * n
+    assert tt.tt_ranks(cores) == g["tt_ranks"]
+    assert sum(G.size for G in cores) == g["storage_per_n"][0] * n
     assert np.abs(tt.tt_full(cores) - A).max() < 1e-13
 
 
