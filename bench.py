@@ -32,6 +32,7 @@ WORKLOADS = {
     "pile40p": "40^3 polydisperse lattice, r~U[0.4,0.6], delta=0.21, mu=0.5, dt=1e-3, 2^20 padded unknowns",
     "pile20": "20^3 monodisperse lattice, r=0.5, mu=0.5, dt=1e-3, 2^17 padded unknowns",
     "pile8": "8^3 monodisperse lattice, r=0.5, mu=0.5, dt=1e-3, 2^13 padded unknowns",
+    "stack16": "16x16 columns of 10 spheres, r=0.5, mu=0.5, dt=1e-3, 2^13 padded unknowns",
 }
 
 
@@ -156,6 +157,7 @@ def job_throughput(local_units, local_ms, world):
 
 
 # ---------------------------------------------------------------------- our arm
+STATUS_NAMES = {0: "ok", -4: "not_converged", -5: "breakdown", -6: "linesearch_fail", -7: "timeout"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pcg<float, void>
 # launch of the 40^3 window, from an ncu capture of this kernel version (caches
 # flushed by ncu before the launch).  Reset to None when the kernel changes.
@@ -234,6 +236,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     step_ms, pcg_ms, iters, outer, relres, refresh_ms = [], [], [], [], [], []
+    status_counts, solved, stepped = {}, 0, 0
     launches = 0
     with ClockSampler(local) as clk:
         time.sleep(0.5)  # let the sampler start before the timed region
@@ -255,10 +258,17 @@ def run_ours(args):
                 outer.append(s.solve.outer)
                 relres.append(s.solve.rel_res)
                 refresh_ms.append(s.ms_refresh)
+                name = STATUS_NAMES.get(s.status, str(s.status))
+                status_counts[name] = status_counts.get(name, 0) + 1
+                # a Newton solve counts when it reached the tolerance; a PDIP step
+                # counts when its line search accepted a step (status OK)
+                solved += int(s.solve.status == binding.QP_OK and s.solve.rel_res <= 1e-8)
+                stepped += int(s.status == binding.QP_OK)
             launches += 1 + 4 * args.window  # init; pre-step, Jacobi diagonal, Krylov kernel, post-step
         torch.cuda.synchronize()
         barrier(world)
-    value, total_ms = job_throughput(float(args.steps * args.window), sum(step_ms), world)
+    value, total_ms = job_throughput(float(solved), sum(step_ms), world)
+    pdip_steps_per_s, _ = job_throughput(float(stepped), sum(step_ms), world)
 
     # roofline of the dominant kernel (persistent PCG)
     nrow = 3 * Nc
@@ -334,7 +344,9 @@ def run_ours(args):
             ap_ms.append(e0.elapsed_time(e1))
         # schedule of qtt_apply: cores d, d-1, ... in passes of two where both ranks of
         # the pair and the rank below are <= 12 (else one); a pass reads r_in * N and
-        # writes r_out * N FP32 values; flops = 2 * 4 r_{k-1} r_k N per core
+        # writes r_out * N FP32 values.  Flops: core k is applied to N/2 column items,
+        # each a (2 r_{k-1}) x (2 r_k) matrix times a 2 r_k vector, i.e. 4 r_{k-1} r_k
+        # multiply-adds = 8 r_{k-1} r_k flops, so 4 r_{k-1} r_k N flops per core
         ap_bytes, ap_passes, k = 0, 0, len(ranks) - 1
         while k >= 1:
             fuse = k >= 2 and max(ranks[k - 1], ranks[k]) <= 12 and \
@@ -343,7 +355,7 @@ def run_ours(args):
             ap_bytes += (ranks[k] + ranks[nxt]) * P * 4
             ap_passes += 1
             k = nxt
-        ap_flops = sum(8 * ranks[k] * ranks[k + 1] * P for k in range(len(ranks) - 1))
+        ap_flops = sum(4 * ranks[k] * ranks[k + 1] * P for k in range(len(ranks) - 1))
         ap_t = statistics.median(ap_ms) / 1e3
         qv = args.window * 1e3 / statistics.mean(q_ms)
         qtt_out = {"value": qv, "unit": UNIT, "factor_vs_jacobi": qv / value,
@@ -397,6 +409,16 @@ def run_ours(args):
     ts_out = time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream) if args.ts_steps > 0 else None
     batch_out = batched_leg(args, binding, workload) if args.batch_scenes > 0 else None
     learned_out = learned_leg(args, binding, workload) if args.learned_steps > 0 else None
+    configs_out = None
+    if args.config_legs:
+        cpu_ok = rank == 0 and not args.no_cpu_baseline
+        configs_out = {
+            "pile8_fp64": config_leg(binding, workload, "pile8", 1e-10, args.window, [(1e-2, 10)], flush, stream,
+                                     cpu=cpu_ok),
+            "stack16_pdip_to_gap": stack_leg(binding, workload, flush, stream, cpu=cpu_ok),
+            "pile20_fp64_qtt": config_leg(binding, workload, "pile20", 1e-8, 4, [(1e-3, 64), (1e-2, 10)], flush,
+                                          stream, reps=2, cpu=cpu_ok),
+        }
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -408,6 +430,8 @@ def run_ours(args):
                    "pdip_iterates": f"each step: cold start, then PDIP iterations 0..{args.window - 1}",
                    "newton_solves_per_step": args.window,
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "newton_solves_converged": solved, "newton_solves_attempted": args.steps * args.window,
+        "pdip_steps_per_s": pdip_steps_per_s, "pdip_step_status_counts": status_counts,
         "krylov_iters_per_solve": statistics.mean(iters), "refinements_per_solve": statistics.mean(outer),
         "max_rel_res": max(relres), "pcg_ms_per_solve": statistics.mean(pcg_ms),
         "qtt_refresh_ms_per_step": statistics.mean(refresh_ms) if qtt else None,
@@ -424,13 +448,14 @@ def run_ours(args):
         "time_stepping": ts_out,
         "batched": batch_out,
         "learned_warm_start": learned_out,
+        "configs": configs_out,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        ctx.pdip_init(st, 1.0)
-        out["cpu_baseline"] = cpu_baseline(scene, gamma, lam, statistics.mean(iters) + statistics.mean(outer))
+        its = gpu_window_iterates(ctx, st, gamma, lam, opts, args.window, ok, Nc)
+        sample = list(range(1, args.window, 2)) if args.workload == "pile40p" else list(range(args.window))
+        out["cpu_baseline"] = cpu_baseline(scene, its, sample)
         if args.cpu_all_cores:
-            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload, gamma, lam,
-                                                                   out["cpu_baseline"]["iterations_per_solve"])
+            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload, its, sample)
     ctx2.close()
     ctx.close()
     if rank == 0:
@@ -495,6 +520,138 @@ def n_apply_leg(binding, ctx, st, Nc, M, P, flush, stream, reps=20):
                         "gbs": nbytes / t / 1e9, "roofline": roof}
     out["note"] = ("median of %d calls, L2 flushed before each; with_state includes the Schur-block "
                    "build from (gamma, lambda)" % reps)
+    return out
+
+
+def config_leg(binding, workload, name, tol, window, qtt_variants, flush, stream, reps=3, cpu=True):
+    """One of the smaller configurations, FP64 throughout: `window` PDIP
+    iterations from the cold start solved with Jacobi-PCG to `tol`, then with the
+    QTT-preconditioned PCG for each (eps, rmax) in `qtt_variants` (S compressed
+    and inverted at every Newton iteration, the inverse warm-started from the
+    previous one, Sec. 3.3), each against the same iterates; plus the oracle's
+    PDIP iteration on the GPU window's own iterates (one host core)."""
+    import torch
+
+    from synth import scene_for
+
+    scene = scene_for(name, 1)
+    ctx = binding.Context()
+    _, con = workload.assemble(ctx, scene)
+    g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+    st = ctx.state(g, lam)
+    ok = (binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL)
+
+    def timed(opts, n):
+        ms, rec = [], []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            one = []
+            e0.record(stream)
+            ctx.pdip_init(st, 1.0)
+            for _ in range(window):
+                one.append(ctx.pdip_step(st, opts, allow=ok))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            rec += one
+        conv = sum(1 for r in rec if r.solve.status == binding.QP_OK and r.solve.rel_res <= tol)
+        return conv / (sum(ms) / 1e3), rec, ms
+
+    jo = ctx.pdip_opts(ctx.solve_opts(tol=tol, maxit=200000))
+    timed(jo, 1)
+    jv, jrec, jms = timed(jo, reps)
+    out = {"workload": f"{name}: {WORKLOADS[name]}", "contacts": con.Nc, "padded_unknowns": con.P, "dtype": "f64",
+           "newton_tol": tol, "pdip_iterates": f"cold start, then PDIP iterations 0..{window - 1}",
+           "jacobi_pcg": {"value": jv, "unit": UNIT, "ms_per_window": statistics.mean(jms),
+                          "krylov_iters_per_solve": statistics.mean(r.solve.iters for r in jrec)},
+           "qtt_pcg": []}
+    for eps, rmax in qtt_variants:
+        so = ctx.solve_opts(binding.QP_QTT_PCG, None, tol=tol, maxit=20000)
+        qo = ctx.pdip_opts(so, qtt_refresh=1, qtt_eps=eps, qtt_rmax=rmax)
+        timed(qo, 1)
+        qv, qrec, qms = timed(qo, 1)
+        ro = ctx.pdip_opts(so, qtt_refresh=0)
+        # re-use across Newton iterations: refresh at the first iteration only
+        ctx.pdip_init(st, 1.0)
+        rr = []
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(window):
+            rr.append(ctx.pdip_step(st, qo if i == 0 else ro, allow=ok))
+        e1.record(stream)
+        e1.synchronize()
+        rms = e0.elapsed_time(e1)
+        rconv = sum(1 for r in rr if r.solve.status == binding.QP_OK and r.solve.rel_res <= tol)
+        out["qtt_pcg"].append({
+            "eps": eps, "rmax": rmax, "value": qv, "unit": UNIT, "factor_vs_jacobi": qv / jv,
+            "refresh_ms": statistics.mean(r.ms_refresh for r in qrec),
+            "solve_ms": statistics.mean(r.solve.ms for r in qrec),
+            "solve_only_factor_vs_jacobi": statistics.mean(r.solve.ms for r in jrec) / statistics.mean(
+                r.solve.ms for r in qrec),
+            "krylov_iters_per_solve": statistics.mean(r.solve.iters for r in qrec),
+            "jacobi_fallbacks": sum(r.solve.fallback for r in qrec),
+            "refresh_once_per_window": {"value": rconv / (rms / 1e3), "factor_vs_jacobi": rconv / (rms / 1e3) / jv,
+                                        "krylov_iters_per_solve": statistics.mean(r.solve.iters for r in rr)}})
+    if cpu:
+        its = gpu_window_iterates(ctx, st, g, lam, jo, window, ok, con.Nc)
+        out["cpu_baseline"] = cpu_baseline(scene, its, list(range(window)), tol)
+    ctx.close()
+    return out
+
+
+def stack_leg(binding, workload, flush, stream, cpu=True):
+    """PDIP to convergence (gap 1e-8 and dual residual 1e-8, Sec. 2.4) on 16 x 16
+    columns of 10 spheres (2560 contacts, 2^13), where every contact carries load
+    and the method converges: FP64 Jacobi-PCG Newton solves to 1e-10."""
+    import torch
+
+    from synth import scene_for
+
+    scene = scene_for("stack16", 1)
+    ctx = binding.Context()
+    _, con = workload.assemble(ctx, scene)
+    g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+    st = ctx.state(g, lam)
+    opts = ctx.pdip_opts(ctx.solve_opts(tol=1e-10, maxit=200000))
+    ms, n, stats = [], 0, None
+    for rep in range(4):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.pdip_init(st, 1.0)
+        stats, n = ctx.pdip_solve(st, opts, gap_tol=1e-8, dual_tol=1e-8, max_iter=200)
+        e1.record(stream)
+        e1.synchronize()
+        if rep:
+            ms.append(e0.elapsed_time(e1))
+    out = {"workload": "stack16: 16x16 columns of 10 spheres, r=0.5, mu=0.5, dt=1e-3, 2^13 padded unknowns",
+           "contacts": con.Nc, "converged": stats.status == binding.QP_OK, "pdip_iterations": n,
+           "eta": stats.eta, "r_dual": stats.r_dual, "ms_per_pdip_solve": statistics.mean(ms),
+           "pdip_solves_per_s": 1e3 / statistics.mean(ms), "newton_solves_per_s": n * 1e3 / statistics.mean(ms)}
+    ctx.close()
+    if cpu:
+        from oracle import krylov, pdip
+
+        c_o, N, r = oracle_data(scene)
+
+        def solver(S, b):
+            x, info = krylov.jacobi_pcg(S, b, tol=1e-10, maxit=100000)
+            return x, info["iters"]
+
+        t0 = time.perf_counter()
+        res = pdip.pdip_solve(N, r, scene.mu, tol_gap=1e-8, tol_dual=1e-8, maxit=200, newton_solver=solver)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 1.0 / el, "unit": "PDIP solves/s", "cores": 1, "kind": "oracle",
+                               "newton_solves_per_s": res.iters / el,
+                               "sample": f"oracle FP64 PDIP loop with Jacobi-PCG to 1e-10, {res.iters} iterations, "
+                                         f"converged={res.converged}, {el:.1f} s"}
     return out
 
 
@@ -732,92 +889,117 @@ def time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream):
 
 
 # ---------------------------------------------------------------------- oracle arm
-def oracle_system(scene, gamma_c=None, lam=None):
-    from oracle import contacts as oc, pdip, qp
+def oracle_data(scene):
+    from oracle import contacts as oc, qp
 
     con = oc.detect(scene)
     D, N, r = qp.qp_data(scene, con)
-    if gamma_c is None:
-        gamma_c, lam = qp.initial_point(con.Nc, scene.mu)
-    f = qp.constraints(gamma_c, scene.mu)
-    t = pdip.NU * 2 * con.Nc / float(-(f @ lam))
-    S = qp.schur_matrix(N, gamma_c, lam, scene.mu)
-    rhs = qp.newton_rhs(N, r, gamma_c, lam, t, scene.mu)
-    return S, rhs
+    return con, N, r
 
 
-def oracle_sample(S, rhs, seconds=12.0):
-    """Run the oracle's Jacobi-PCG for about `seconds`; returns (iters, elapsed)."""
-    from oracle import krylov
+def oracle_pdip_times(scene, iterates, tol=1e-8, data=None):
+    """The oracle's PDIP iteration (Sec. 2.4: Schur blocks and rhs, Jacobi-PCG
+    Newton solve to `tol`, dlambda, ratio test, backtracking, update) timed at
+    each given (gamma, lambda) iterate (compact layout).  Returns a list of
+    (seconds, krylov iterations)."""
+    from oracle import krylov, pdip
 
-    # calibrate: 20 iterations
-    t0 = time.perf_counter()
-    krylov.jacobi_pcg(S, rhs, tol=1e-30, maxit=20)
-    per = (time.perf_counter() - t0) / 20
-    n = max(20, int(seconds / per))
-    t0 = time.perf_counter()
-    _, info = krylov.jacobi_pcg(S, rhs, tol=1e-8, maxit=n)
-    el = time.perf_counter() - t0
-    return info, el
+    con, N, r = data or oracle_data(scene)
+
+    def solver(S, b):
+        x, info = krylov.jacobi_pcg(S, b, tol=tol, maxit=100000)
+        return x, info["iters"]
+
+    out = []
+    for g, lam in iterates:
+        t0 = time.perf_counter()
+        _, _, info = pdip.pdip_step(N, r, scene.mu, g, lam, newton_solver=solver)
+        out.append((time.perf_counter() - t0, info.krylov_iters))
+    return out
 
 
-def cpu_baseline(scene, gamma=None, lam=None, iters_per_solve=None):
-    from oracle import qp
+def oracle_window(scene, window, tol=1e-8, data=None):
+    """The oracle's own PDIP window: iterates 0..window-1 from the cold start."""
+    from oracle import krylov, pdip, qp
 
-    g_c = l_c = None
-    if gamma is not None:
-        Nc = lam.numel() // 2
-        g_c = qp.from_padded(gamma.cpu().numpy(), Nc, 3)
-        l_c = lam.cpu().numpy()
-    S, rhs = oracle_system(scene, g_c, l_c)
-    info, el = oracle_sample(S, rhs)
-    per_it = el / max(1, info["iters"])
-    need = info["iters"] if info["converged"] else (iters_per_solve or info["iters"])
-    return {"value": 1.0 / (per_it * need), "unit": UNIT, "cores": 1, "kind": "oracle", "iterations_per_solve": need,
-            "sample": (f"oracle FP64 Jacobi-PCG (numpy/scipy, 1 thread) on the same Newton system: {info['iters']} "
-                       f"iterations in {el:.1f} s ({'converged' if info['converged'] else 'capped'}); solves/s = "
-                       f"1/(s per iteration x {need:.0f} iterations per solve"
-                       f"{'' if info['converged'] else ', the GPU count'})")}
+    con, N, r = data or oracle_data(scene)
+
+    def solver(S, b):
+        x, info = krylov.jacobi_pcg(S, b, tol=tol, maxit=100000)
+        return x, info["iters"]
+
+    g, lam = qp.initial_point(con.Nc, scene.mu)
+    its = []
+    for _ in range(window):
+        its.append((g.copy(), lam.copy()))
+        g, lam, _ = pdip.pdip_step(N, r, scene.mu, g, lam, newton_solver=solver)
+    return its
+
+
+def gpu_window_iterates(ctx, st, gamma, lam, opts, window, ok, Nc):
+    """(gamma, lambda) before each PDIP iteration of one window, in the compact
+    layout the oracle uses (read back from the device, untimed)."""
+    idx = None
+    out = []
+    ctx.pdip_init(st, 1.0)
+    for _ in range(window):
+        g = gamma.cpu().numpy()
+        if idx is None:
+            import numpy as np
+
+            idx = (3 * np.arange(Nc)[:, None] + np.arange(3)[None, :]).reshape(-1)
+        out.append((g[idx].copy(), lam.cpu().numpy().copy()))
+        ctx.pdip_step(st, opts, allow=ok)
+    return out
+
+
+def cpu_baseline(scene, iterates, sample, tol=1e-8):
+    """The oracle as it stands on one host core: its PDIP iteration at the GPU
+    window's own iterates `sample` (indices into `iterates`)."""
+    times = oracle_pdip_times(scene, [iterates[i] for i in sample], tol)
+    el = sum(t for t, _ in times)
+    return {"value": len(times) / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "iterations_per_solve": statistics.mean(k for _, k in times),
+            "sample": (f"oracle FP64 PDIP iteration (numpy/scipy, 1 thread; Schur blocks, rhs, Jacobi-PCG to "
+                       f"{tol:g}, update) at PDIP iterates {list(sample)} of the GPU's own timed window "
+                       f"(read back after timing): {len(times)} iterations in {el:.1f} s, "
+                       f"{statistics.mean(k for _, k in times):.0f} CG iterations per solve; one Newton solve "
+                       f"per PDIP iteration")}
 
 
 def _oracle_worker(job):
-    """One host core of the all-cores CPU baseline: build the oracle's Newton
-    system, then run its Jacobi-PCG solve to 1e-8 repeatedly for `seconds`.
-    Returns (iterations, elapsed seconds of the solving window)."""
-    workload, seed, gamma_c, lam, seconds = job
-    from oracle import krylov
+    """One host core of the all-cores CPU baseline: the oracle's PDIP iteration
+    at one iterate, repeated for `seconds`.  Returns (iterations, seconds)."""
+    workload, seed, it, tol, seconds = job
     from synth import scene_for
 
-    S, rhs = oracle_system(scene_for(workload, seed=seed), gamma_c, lam)
-    its, t0 = 0, time.perf_counter()
+    scene = scene_for(workload, seed=seed)
+    data = oracle_data(scene)
+    n, t0 = 0, time.perf_counter()
     while True:
-        _, info = krylov.jacobi_pcg(S, rhs, tol=1e-8, maxit=20000)
-        its += info["iters"]
+        oracle_pdip_times(scene, [it], tol, data)
+        n += 1
         el = time.perf_counter() - t0
         if el >= seconds:
-            return its, el
+            return n, el
 
 
-def cpu_baseline_all_cores(workload, gamma, lam, iters_per_solve, seconds=5.0):
-    """The oracle on every host core: one process per core (spawned, one thread
-    each), each solving the same Newton system repeatedly; the job's rate is the
-    sum of the per-core iteration rates over the iterations of one solve."""
+def cpu_baseline_all_cores(workload, iterates, sample, tol=1e-8, seconds=10.0):
+    """The oracle on every host core: one spawned single-thread process per core,
+    process i repeating the PDIP iteration at iterate sample[i mod len(sample)];
+    the job's rate is the sum of the per-process rates."""
     import concurrent.futures as cf
     import multiprocessing as mp
 
-    from oracle import qp
-
-    Nc = lam.numel() // 2
-    g_c = qp.from_padded(gamma.cpu().numpy(), Nc, 3)
-    l_c = lam.cpu().numpy()
     cores = os.cpu_count() or 1
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"
+    jobs = [(workload, 1, iterates[sample[i % len(sample)]], tol, seconds) for i in range(cores)]
     try:
         # a worker that dies breaks the executor (an error, not a hang)
         with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
-            res = list(ex.map(_oracle_worker, [(workload, 1, g_c, l_c, seconds)] * cores))
+            res = list(ex.map(_oracle_worker, jobs))
     except Exception as e:  # reported in the line instead of failing the bench
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": repr(e)[:200]}
     finally:
@@ -826,45 +1008,48 @@ def cpu_baseline_all_cores(workload, gamma, lam, iters_per_solve, seconds=5.0):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    rate = sum(i / e for i, e in res)
-    return {"value": rate / iters_per_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle FP64 Jacobi-PCG (numpy/scipy), {cores} spawned processes of one thread, each "
-                       f"solving the same Newton system to 1e-8 repeatedly for {seconds:.0f} s "
-                       f"({sum(i for i, _ in res)} iterations in all); solves/s = sum of per-process "
-                       f"iterations/s / {iters_per_solve:.0f} iterations per solve")}
+    rate = sum(n / e for n, e in res)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle FP64 PDIP iteration (numpy/scipy), {cores} spawned processes of one thread, "
+                       f"process i repeating PDIP iterate {list(sample)}[i mod {len(sample)}] of the GPU's window "
+                       f"for {seconds:.0f} s ({sum(n for n, _ in res)} iterations in all); rate = sum of "
+                       f"per-process iterations/s (one Newton solve each)")}
 
 
 def run_reference(args):
-    """The oracle as it stands, on the host cores: each step solves the first Newton
-    system of the workload (PDIP iteration 0 from the cold start) with the oracle's
-    FP64 Jacobi-PCG to 1e-8, a bounded sample of the GPU step's eight solves."""
+    """The oracle as it stands, on the host cores, on the benchmark's workload:
+    the oracle computes its own PDIP window (iterates 0..window-1 from the cold
+    start, untimed set-up); timed step j is the oracle's PDIP iteration at
+    iterate j mod window, one Newton solve each, a bounded sample of the GPU
+    step's `window` iterations."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import krylov
     from synth import scene_for
 
     scene = scene_for(args.workload, seed=1)
-    S, rhs = oracle_system(scene)
-    for _ in range(args.warmup):
-        krylov.jacobi_pcg(S, rhs, tol=1e-8, maxit=2000)
-    times, its, conv = [], [], True
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        _, info = krylov.jacobi_pcg(S, rhs, tol=1e-8, maxit=20000)
-        times.append(time.perf_counter() - t0)
-        its.append(info["iters"])
-        conv = conv and info["converged"]
+    tol = 1e-8 if args.workload != "pile8" else 1e-10
+    data = oracle_data(scene)
+    its = oracle_window(scene, args.window, tol, data)
+    times, kry = [], []
+    for j in range(args.warmup + args.steps):
+        (t, k), = oracle_pdip_times(scene, [its[j % args.window]], tol, data)
+        if j >= args.warmup:
+            times.append(t)
+            kry.append(k)
     per = statistics.mean(times)
     value = 1.0 / per
+    sample = (f"oracle FP64 PDIP iteration (numpy/scipy, 1 thread; Schur blocks, rhs, Jacobi-PCG to {tol:g}, "
+              f"update) at its own iterates j mod {args.window} of the cold-start window; "
+              f"{statistics.mean(kry):.0f} CG iterations per solve")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "precond": "jacobi",
-                      "newton_tol": 1e-8, "pdip_iterates": "PDIP iteration 0 from the cold start"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"oracle FP64 Jacobi-PCG (numpy/scipy, 1 thread): one Newton solve per step, "
-                                      f"{statistics.mean(its):.0f} iterations, {'converged' if conv else 'capped'}"},
+                      "newton_tol": tol,
+                      "pdip_iterates": f"PDIP iterations 0..{args.window - 1} from the cold start (the GPU "
+                                       f"step's window), one per timed step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -888,6 +1073,8 @@ def main():
     ap.add_argument("--ts-qtt", type=int, default=1, help="time-stepping leg: measure the QTT refresh reuse (0: skip)")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
     ap.add_argument("--learned-steps", type=int, default=200, help="training epochs of the learned leg (0: skip)")
+    ap.add_argument("--config-legs", type=int, default=1,
+                    help="also run the 8^3 FP64, the columns PDIP-to-gap and the 20^3 FP64 QTT legs (0: skip)")
     ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],
                     help="Krylov method of the QTT leg (the paper uses BiCGSTAB)")
     ap.add_argument("--qtt-maxit", type=int, default=2000,

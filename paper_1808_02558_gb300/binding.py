@@ -136,11 +136,23 @@ def load(path: str = LIB_PATH):
 
 
 def qtt_apply_f32_noalloc(ranks: list, cores, x, y, stream=None) -> int:
-    """Context-free, allocation-free y = A x (float32 cores and vectors); returns the status."""
+    """Context-free, allocation-free y = A x (float32 cores and vectors); returns the status.
+
+    The C entry point sees raw device pointers only, so the buffer sizes are
+    checked here: x and y hold 2^d float32 values, cores holds
+    sum_k r_{k-1} * 4 * r_k float32 values, all contiguous CUDA tensors."""
     import torch
 
     lib = load()
     d = len(ranks) - 1
+    if d < 1 or any(int(v) < 1 for v in ranks):
+        raise ValueError("ranks must be d + 1 >= 2 positive integers")
+    need = sum(int(ranks[k]) * 4 * int(ranks[k + 1]) for k in range(d))
+    for name, t, n in (("cores", cores, need), ("x", x, 1 << d), ("y", y, 1 << d)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if t.numel() != n:
+            raise ValueError(f"{name} has {t.numel()} values, expected {n}")
     r = (C.c_int * (d + 1))(*ranks)
     s = torch.cuda.current_stream() if stream is None else stream
     return lib.qtt_apply_f32_noalloc(d, r, C.c_void_p(cores.data_ptr()), C.c_void_p(x.data_ptr()),

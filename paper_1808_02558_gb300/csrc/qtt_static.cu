@@ -89,8 +89,12 @@ extern "C" int qtt_apply_f32_noalloc(int d, const int* ranks_host, const float* 
   const float* in = x;
   for (int k = d; k >= 1; --k) {
     float* out = (k == 1) ? y : (((d - k) & 1) ? w1 : w0);
-    k_qtt_step_noalloc<<<(int)blocks, 256, 0, st>>>(q, k, in, out, items);
-    if (cudaGetLastError() != cudaSuccess) return QP_CUDA_ERROR;
+    // cudaLaunchKernel returns this launch's own status: an earlier error of the
+    // caller is neither reported as ours nor cleared
+    void* args[] = {&q, &k, (void*)&in, &out, (void*)&items};
+    if (cudaLaunchKernel((const void*)k_qtt_step_noalloc, dim3((unsigned)blocks), dim3(256), args, 0, st) !=
+        cudaSuccess)
+      return QP_CUDA_ERROR;
     in = out;
   }
   return QP_OK;

@@ -117,16 +117,41 @@ def lattice_scene(n: int, seed: int, polydisperse: bool = False, *, mu: float = 
                  omega=omega, radius=radius, mu=mu, dt=dt, delta=d, seed=seed)
 
 
-# Named workloads: the small FP64 pile, the 20^3 pile and the 40^3 polydisperse pile.
+def column_scene(nx: int, height: int, seed: int, *, lateral: float = 1.03, spacing: float = 0.98,
+                 jitter: float = 0.01, vel_sigma: float = 0.1, mu: float = 0.5, dt: float = 1e-3,
+                 z0: float = 0.49, name: str | None = None) -> Scene:
+    """nx x nx columns of `height` spheres (radius 0.5) standing on the floor.
+
+    Columns are `lateral` apart (wider than a diameter plus twice the jitter, so
+    no two columns touch) and spheres in a column `spacing` apart, so every
+    contact is a floor contact or a vertical pair carrying the weight above it;
+    jitter, velocities and the rest of the recipe are those of lattice_scene.
+    Body id = i + nx*j + nx*nx*k for column (i, j), level k.
+    """
+    M = nx * nx * height
+    k, j, i = np.meshgrid(np.arange(height), np.arange(nx), np.arange(nx), indexing="ij")
+    site = np.stack([i.ravel() * lateral, j.ravel() * lateral, k.ravel() * spacing], axis=1).astype(np.float64)
+    jit = (2.0 * splitmix64_uniform(seed, 1, 3 * M) - 1.0).reshape(M, 3) * jitter
+    pos = site + np.array([0.0, 0.0, z0]) + jit
+    vel = normal_vector(seed, 2, 3 * M, vel_sigma).reshape(M, 3)
+    return Scene(name=name or f"columns{nx}x{height}-s{seed}", pos=pos, vel=vel, omega=np.zeros((M, 3)),
+                 radius=np.full(M, 0.5), mu=mu, dt=dt, delta=0.0, seed=seed)
+
+
+# Named workloads: the small FP64 pile, the 20^3 pile, the 40^3 polydisperse pile,
+# and 16 x 16 columns of 10 spheres (every contact loaded; 2560 contacts, 2^13).
 SCENES = {
     "pile8": dict(n=8, polydisperse=False),
     "pile20": dict(n=20, polydisperse=False),
     "pile40p": dict(n=40, polydisperse=True),
+    "stack16": dict(columns=16, height=10),
 }
 
 
 def scene_for(name: str, seed: int = 1) -> Scene:
     spec = SCENES[name]
+    if "columns" in spec:
+        return column_scene(spec["columns"], spec["height"], seed, name=f"{name}-s{seed}")
     return lattice_scene(spec["n"], seed, spec["polydisperse"], name=f"{name}-s{seed}")
 
 

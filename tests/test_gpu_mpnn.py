@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_common import Problem, relerr, to_np
+from gpu_common import Problem, assert_close, relerr, to_np
 from oracle import mpnn, qp
 from paper_1808_02558_gb300 import binding, learned
 from synth import lattice_scene, scene_for
@@ -41,6 +41,8 @@ def test_forward_matches_oracle(ctx):
     out = torch.empty(3 * pb.Nc, dtype=torch.float32, device="cuda")
     pb.ctx.mpnn_forward(params, SCALE, out)
     want, _ = mpnn.forward(theta, x, pb.oc.a, pb.oc.b, pb.scene.M)
+    # FP32 width-64 layers against FP64 with the same bf16 weights
+    assert_close(to_np(out), want.reshape(-1), 1e-4, floor_rel=1e-2, what="forward")
     assert relerr(to_np(out).astype(np.float64), want.reshape(-1)) <= 1e-5
 
 
@@ -56,7 +58,7 @@ def test_backward_matches_oracle(ctx):
     k = 0
     for s in mpnn.SHAPES:
         n = int(np.prod(s))
-        assert relerr(to_np(g)[k:k + n].astype(np.float64), want[k:k + n]) <= 1e-3
+        assert_close(to_np(g)[k:k + n], want[k:k + n], 1e-3, floor_rel=1e-2, what=f"gradient block {s}")
         k += n
 
 
@@ -71,7 +73,9 @@ def test_adam_step(ctx):
     m1 = 0.9 * m0 + 0.1 * gg
     v1 = 0.999 * v0 + 0.001 * gg * gg
     p1 = p0 - 1e-2 * (m1 / (1 - 0.9 ** 3)) / (np.sqrt(v1 / (1 - 0.999 ** 3)) + 1e-8)
-    assert relerr(to_np(params).astype(np.float64), p1) <= 1e-6
+    # the update itself, entry by entry: the FP32 bias correction 1 - beta2^3 cancels to
+    # about 2e-5 relative, so the step is checked to 1e-4 of max(|dp_i|, 1e-3 max|dp|)
+    assert_close(to_np(params).astype(np.float64) - p0, p1 - p0, 1e-4, floor_rel=1e-3, what="Adam update")
 
 
 def test_warm_start_matches_oracle(ctx):
@@ -82,8 +86,8 @@ def test_warm_start_matches_oracle(ctx):
     st = pb.ctx.state(g, lam)
     pb.ctx.mpnn_warm_start(st, out, 2.5, gn_min=1e-2, shrink=0.9)
     wg, wl = mpnn.warm_start(to_np(out).astype(np.float64).reshape(-1, 3), 2.5, pb.scene.mu, 1e-2, 0.9)
-    assert relerr(pb.unpad(to_np(g)), wg) <= 1e-14
-    assert relerr(to_np(lam), wl) <= 1e-12
+    assert_close(pb.unpad(to_np(g)), wg, 1e-14, floor_rel=1e-6, what="warm-start gamma")
+    assert_close(to_np(lam), wl, 1e-12, floor_rel=1e-9, what="warm-start lambda")
 
 
 def test_training_fits_pdip_iterates(ctx):

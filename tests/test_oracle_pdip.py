@@ -112,3 +112,59 @@ def test_kkt_against_brute_force(kind):
     q = lambda x: 0.5 * x @ (N @ x) + r @ x
     assert abs(q(g) - q(gb)) <= 1e-7 * max(1.0, abs(q(gb)))
     assert np.allclose(D @ g, D @ gb, rtol=0, atol=1e-5 * max(1.0, np.abs(D @ gb).max()))
+
+
+def test_column_at_rest_matches_linear_solve():
+    """A vertical column of spheres with no jitter and no velocity: every contact
+    is loaded along z, so the CCP solution has gamma_t = 0 and normal impulses
+    that make every post-step relative normal velocity exactly -Phi/dt (Eq.
+    complementarity_disc with gamma_n > 0).  For the chain that is a small
+    linear system in the impulses, written here from the momentum balance of
+    each sphere (Eq. force_balance_disc), independently of N and r."""
+    from synth import column_scene
+
+    h = 6
+    s = column_scene(1, h, 3, jitter=0.0, vel_sigma=0.0)
+    c = oc.detect(s)
+    assert c.Nc == h
+    _, N, r = qp.qp_data(s, c)
+    res = pdip.pdip_solve(N, r, s.mu, tol_gap=1e-12, tol_dual=1e-9, maxit=100)
+    assert res.converged
+    m, dt, g = s.mass[0], s.dt, s.gravity[2]
+    below = {int(b): k for k, b in enumerate(c.b)}      # contact under sphere j
+    A = np.zeros((h, h))
+    rhs = np.zeros(h)
+    # w_j = dt g + (gamma_below(j) - gamma_below(j+1)) / m;  u_c = w_j - w_{j-1} + Phi_c / dt = 0
+    for j in range(h):
+        k = below[j]
+        for sgn, jj in ((1.0, j), (-1.0, j - 1)):
+            if jj < 0:
+                continue
+            A[k, below[jj]] += sgn / m
+            if jj + 1 < h:
+                A[k, below[jj + 1]] -= sgn / m
+            rhs[k] -= sgn * dt * g
+        rhs[k] -= c.phi[k] / dt
+    want_n = np.linalg.solve(A, rhs)
+    assert np.all(want_n > 0)
+    assert np.allclose(res.gamma[0::3], want_n, rtol=1e-8, atol=0)
+    assert np.abs(res.gamma[1::3]).max() <= 1e-8 * want_n.max()
+    assert np.abs(res.gamma[2::3]).max() <= 1e-8 * want_n.max()
+
+
+def test_column_scene_converges_to_kkt():
+    """The 16 x 16 x 10 column scene (every contact loaded, no cone apex): the
+    PDIP reaches gap 1e-8 and dual residual 1e-8, and the KKT conditions hold."""
+    from synth import scene_for
+
+    s = scene_for("stack16", 1)
+    c = oc.detect(s)
+    _, N, r = qp.qp_data(s, c)
+    res = pdip.pdip_solve(N, r, s.mu, tol_gap=1e-8, tol_dual=1e-8, maxit=100)
+    assert res.converged and res.iters <= 60
+    g = res.gamma.reshape(-1, 3)
+    assert np.all(g[:, 0] > 0) and np.all(np.hypot(g[:, 1], g[:, 2]) < s.mu * g[:, 0])
+    u = (N @ res.gamma + r).reshape(-1, 3)
+    # dual cone: u_n >= mu ||u_t|| up to the residual; complementarity gamma . u ~ 0
+    assert np.all(u[:, 0] + 1e-6 >= s.mu * np.hypot(u[:, 1], u[:, 2]) - 1e-6)
+    assert abs(float((g * u).sum())) <= 1e-6 * float(np.abs(g).sum())
