@@ -656,39 +656,48 @@ def stack_leg(binding, workload, flush, stream, cpu=True):
 
 
 def learned_leg(args, binding, workload):
-    """Learned warm start: the network is trained on the PDIP iterates the
-    library itself produces (12 iterations from the cold start) on 8^3 piles of
-    seeds 2..9, then starts the PDIP of the unseen seed 1 (cold start as the
-    fallback); reported: the surrogate gap and dual residual after each of 12
-    PDIP iterations from the cold and the learned start."""
+    """Learned warm start: the network is trained on the converged PDIP solutions
+    (gap and dual residual 1e-8) that the library itself computes for 16 x 16 x
+    10 column scenes of seeds 2..9, then starts the PDIP of unseen seeds (1, 10,
+    11), with the cold start as the fallback (restart from the cold start when
+    the PDIP from the learned start has not converged within the training
+    scenes' largest cold-start count).  Reported per unseen scene: PDIP
+    iterations and device time to convergence from the cold and from the
+    learned start (network inference included)."""
     import torch
 
     from paper_1808_02558_gb300 import learned
     from synth import scene_for
 
-    K = 12
+    scale = [1.0, 1.0, 1.0, 0.05, 0.05, 0.05, 0.05, 2.0]
+    stream = torch.cuda.current_stream()
 
     def system(seed):
-        sc = scene_for("pile8", seed)
+        sc = scene_for("stack16", seed)
         c = binding.Context()
         _, con = workload.assemble(c, sc)
         g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
         lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
-        return c, con, g, lam, c.state(g, lam)
+        rows = (3 * torch.arange(con.Nc, device="cuda")[:, None] + torch.arange(3, device="cuda")[None, :]).reshape(-1)
+        return c, con, g, lam, c.state(g, lam), rows
 
-    opts_of = lambda c: c.pdip_opts(c.solve_opts(tol=1e-10, maxit=200000))
-    ok = (binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL)
-    train = []
-    for seed in range(2, 10):
-        c, con, g, lam, st = system(seed)
+    def cold(c, st):
+        opts = c.pdip_opts(c.solve_opts(tol=1e-10, maxit=200000))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         c.pdip_init(st, 1.0)
-        o = opts_of(c)
-        for _ in range(K):
-            c.pdip_step(st, o, allow=ok)
-        idx = torch.arange(con.Nc, device="cuda")
-        rows = (3 * idx[:, None] + torch.arange(3, device="cuda")[None, :]).reshape(-1)
+        stats, n = c.pdip_solve(st, opts, gap_tol=1e-8, dual_tol=1e-8, max_iter=200)
+        e1.record(stream)
+        e1.synchronize()
+        return opts, n, stats, e0.elapsed_time(e1)
+
+    train, cold_its = [], []
+    for seed in range(2, 10):
+        c, con, g, lam, st, rows = system(seed)
+        _, n, stats, _ = cold(c, st)
+        cold_its.append(n)
         train.append((c, g[rows].clone()))
-    scale = [1.0, 1.0, 1.0, 0.05, 5.0, 5.0, 5.0, 2.0]
     out_scale = float(torch.cat([t[0::3] for _, t in train]).mean())
     net = learned.WarmStartNet(11, scale, out_scale)
     t0 = time.perf_counter()
@@ -698,38 +707,33 @@ def learned_leg(args, binding, workload):
             losses.append(net.train_step(c, t, 1e-3))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-
-    def trajectory(c, st):
-        o = opts_of(c)
-        hist = []
-        for _ in range(K):
-            c.pdip_step(st, o, allow=ok)
-            hist.append(c.pdip_measure(st))
-        return hist
-
-    c, con, g, lam, st = system(1)
-    c.pdip_init(st, 1.0)
-    cold0 = c.pdip_measure(st)
-    cold = trajectory(c, st)
-    gn_min = 1e-3 * out_scale
-    used, _, start0 = net.start(c, st, con.Nc, gn_min=gn_min)
-    policy = trajectory(c, st)
-    net.warm_start(c, st, con.Nc, gn_min)  # the learned start without the fallback
-    forced = trajectory(c, st)
-    target_gap = cold[-1][0]
-    reach = next((i + 1 for i, (e, _) in enumerate(forced) if e <= target_gap), None)
-    for cc, _ in train:
-        cc.close()
-    c.close()
-    return {"train": {"scenes": "pile8 seeds 2..9", "targets": f"PDIP iterate {K} from the cold start",
+    evals = []
+    for seed in (1, 10, 11):
+        c, con, g, lam, st, rows = system(seed)
+        opts, n_cold, s_cold, ms_cold = cold(c, st)
+        g_cold = g[rows].clone()
+        cold(c, st)  # warm-up of the timed pair
+        _, n_cold, s_cold, ms_cold = cold(c, st)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        used, n_l, s_l = net.solve(c, st, con.Nc, opts, gn_min=1e-3 * out_scale, cap=max(cold_its))
+        e1.record(stream)
+        e1.synchronize()
+        dev = float(((g[rows] - g_cold).abs() / g_cold.abs().clamp_min(1e-300)).max())
+        evals.append({"seed": seed, "cold_iters": n_cold, "cold_ms": ms_cold, "learned_iters": n_l,
+                      "learned_ms": e0.elapsed_time(e1), "start_used": used,
+                      "converged": s_l.status == binding.QP_OK, "eta": s_l.eta, "r_dual": s_l.r_dual,
+                      "max_rel_impulse_diff_vs_cold": dev})
+        c.close()
+    for c, _ in train:
+        c.close()
+    return {"train": {"scenes": "stack16 seeds 2..9", "targets": "converged PDIP solutions (gap, dual 1e-8)",
                       "steps": len(losses), "first_loss": losses[0], "final_loss": losses[-1],
-                      "seconds": t_train, "out_scale": out_scale},
-            "eval": {"scene": "pile8 seed 1 (unseen)", "start_used": used,
-                     "cold_start": {"eta": cold0[0], "r_dual": cold0[1]},
-                     "learned_start": {"eta": start0[0], "r_dual": start0[1]},
-                     "cold_eta_r_dual": cold, "with_fallback_eta_r_dual": policy,
-                     "learned_forced_eta_r_dual": forced,
-                     "learned_forced_iters_to_cold_final_gap": reach}}
+                      "seconds": t_train, "out_scale": out_scale, "cold_iters": cold_its},
+            "eval": evals,
+            "iters_saved_mean": statistics.mean(e["cold_iters"] - e["learned_iters"] for e in evals),
+            "speedup_mean": statistics.mean(e["cold_ms"] / e["learned_ms"] for e in evals)}
 
 
 def batched_leg(args, binding, workload):
@@ -1072,7 +1076,7 @@ def main():
     ap.add_argument("--ts-steps", type=int, default=3, help="time steps of the time-stepping leg (0: skip)")
     ap.add_argument("--ts-qtt", type=int, default=1, help="time-stepping leg: measure the QTT refresh reuse (0: skip)")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
-    ap.add_argument("--learned-steps", type=int, default=200, help="training epochs of the learned leg (0: skip)")
+    ap.add_argument("--learned-steps", type=int, default=300, help="training epochs of the learned leg (0: skip)")
     ap.add_argument("--config-legs", type=int, default=1,
                     help="also run the 8^3 FP64, the columns PDIP-to-gap and the 20^3 FP64 QTT legs (0: skip)")
     ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],

@@ -740,6 +740,7 @@ struct PcgArgs {
   void* xb;                 // BiCGSTAB vectors (type T), 5 * P
   int krylov;               // QP_CG or QP_BICGSTAB
   int direct;               // QTT direct mode: the inner solve is one application of X
+  int reliable;             // FP32 Jacobi-CG with reliable updates instead of restarted refinement
   int rec_cache;            // incidences of a block whose gather geometry is cached in shared memory (0: none)
   double tol, inner_tol;
   int maxit, max_outer;
@@ -995,6 +996,195 @@ __device__ int inner_pcg(const PcgArgs& A, const GatherPlan& pl, double tol, int
   return 1;
 }
 
+// Mixed-precision Jacobi-PCG with reliable updates (residual replacement; van
+// der Vorst and Ye, SIAM J. Sci. Comput. 22 (2000); its mixed-precision use in
+// Clark et al., Comput. Phys. Commun. 181 (2010)).  The FP32 CG recursion runs
+// without restarts on S e = r, r = (rhs - S x) / scale.  Whenever its
+// recurrence residual has fallen by inner_tol since the last replacement (or
+// says the target is reached), the FP32 increment is added to the FP64
+// solution x, the true residual rhs - S x is formed in FP64 and replaces the
+// FP32 residual (rescaled to unit norm), and the search direction is kept:
+// with r and z in the new units, p_old in the old ones,
+//   p = z + beta p_old,  beta = (r.z)_new / (r.z)_old * (scale_new / scale_old).
+// An outer restart per refinement would discard the Krylov space each time.
+// Returns 0 converged (true FP64 residual <= tol ||rhs||), 1 cap reached,
+// 2 breakdown, -1 barrier failure; `repl` counts FP64 residual evaluations.
+__device__ int pcg_reliable(const PcgArgs& A, const GatherPlan& pl, double bnorm, int& iters, int& repl,
+                            double& rel) {
+  using T = float;
+  const SysView<T>& s = A.s32;
+  const SysView<double>& s64 = A.s64;
+  T* e = static_cast<T*>(A.e);
+  T* r = static_cast<T*>(A.r);
+  T* z = static_cast<T*>(A.z);
+  T* q = static_cast<T*>(A.q);
+  T* pold = static_cast<T*>(A.p);        // p_{k-1}
+  T* pnew = static_cast<T*>(A.q) + A.P;  // p_k, written by the contact pass
+  const T* dinv = static_cast<const T*>(A.dinv);
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nrow = A.nrow;
+  const unsigned nb = gridDim.x;
+  const double target = A.tol * bnorm;
+  double scale = bnorm;
+  T a0[1] = {};
+  for (long long i = tid; i < nrow; i += gsz) {
+    const T ri = (T)(A.rhs[i] / scale);
+    r[i] = ri;
+    e[i] = 0;
+    const T zi = dinv[i] * ri;
+    z[i] = zi;
+    a0[0] += ri * zi;
+  }
+  block_partials<1, T, T>(a0, A.partial, 0);
+  T t0[1];
+  if (!grid_barrier_total<1, T>(A.ctl, nb, A.partial, 0, t0)) return -1;
+  T rz = t0[0];
+  const T drop2 = (T)(A.inner_tol * A.inner_tol);
+  T beta = 0;
+  bool first = true;
+  // x += scale e (FP64); r64 = rhs - S x; r = r64 / ||r64||, e = 0, z = M^-1 r.
+  // Returns 0 converged, 1 cap, -1 barrier failure, 3 continue (rz_out = r.z).
+  auto replace = [&](T& rz_out) -> int {
+    for (long long i = tid; i < nrow; i += gsz) A.x[i] += scale * (double)e[i];
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    gather_all(s64, plain<double>(A.x), pl);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    apply_all(s64, plain<double>(A.x), A.q64, pl, (double*)nullptr);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    double r2[1] = {0.0};
+    for (long long i = tid; i < nrow; i += gsz) {
+      const double ri = A.rhs[i] - A.q64[i];
+      A.r64[i] = ri;
+      r2[0] += ri * ri;
+    }
+    block_partials<1>(r2, A.partial, 7);
+    if (!grid_barrier(A.ctl, nb)) return -1;
+    const double rn = sqrt(grid_total(A.partial, 7));
+    ++repl;
+    rel = rn / bnorm;
+    if (rel <= A.tol) return 0;
+    if (iters >= A.maxit || repl >= A.max_outer) return 1;
+    T a4[1] = {};
+    for (long long i = tid; i < nrow; i += gsz) {
+      const T ri = (T)(A.r64[i] / rn);
+      r[i] = ri;
+      e[i] = 0;
+      const T zi = dinv[i] * ri;
+      z[i] = zi;
+      a4[0] += ri * zi;
+    }
+    block_partials<1, T, T>(a4, A.partial, 5);
+    T t4[1];
+    if (!grid_barrier_total<1, T>(A.ctl, nb, A.partial, 5, t4)) return -1;
+    rz_out = t4[0];
+    beta = (T)((double)t4[0] / (double)rz * (rn / scale));  // the kept direction in the new units
+    scale = rn;
+    return 3;
+  };
+  for (;;) {
+    if (iters >= A.maxit) return 1;
+    bool broke = !(rz > T(0));
+    T al = 0;
+    if (!broke) {
+      const Operand<T> dir{z, first ? nullptr : pold, beta};
+      // q = S p_k (p_k formed on the fly, stored by the contact pass)
+      gather_all(s, dir, pl);
+      if (!grid_barrier(A.ctl, nb)) return -1;
+      T a2[1] = {apply_all(s, dir, q, pl, pnew)};
+      block_partials<1, T, T>(a2, A.partial, 2);
+      T t2[1];
+      __shared__ T s_alpha_r;
+      if (!grid_barrier_total<1, T>(A.ctl, nb, A.partial, 2, t2,
+                                    [&](const T* t) { s_alpha_r = t[0] > T(0) ? rz / t[0] : T(0); }))
+        return -1;
+      broke = !(t2[0] > T(0));
+      al = s_alpha_r;
+    }
+    if (broke) {
+      // breakdown at the FP32 rounding level: restart the direction from the
+      // true residual (a breakdown before any progress is reported)
+      if (iters == 0) return 2;
+      T rzr;
+      const int st = replace(rzr);
+      if (st != 3) return st;
+      rz = rzr;
+      beta = 0;
+      first = true;
+      continue;
+    }
+    // e += alpha p, r -= alpha q, z = M^-1 r: four rows per thread (float4),
+    // each block on an equal share, all loads of a pass before any store
+    T a3[2] = {};
+    {
+      const long long n4 = nrow >> 2;
+      const float4* P4 = reinterpret_cast<const float4*>(pnew);
+      const float4* Q4 = reinterpret_cast<const float4*>(q);
+      const float4* D4 = reinterpret_cast<const float4*>(dinv);
+      float4* E4 = reinterpret_cast<float4*>(e);
+      float4* R4 = reinterpret_cast<float4*>(r);
+      float4* Z4 = reinterpret_cast<float4*>(z);
+      const long long u0 = n4 * blockIdx.x / gridDim.x, u1 = n4 * (blockIdx.x + 1) / gridDim.x;
+      const long long bs = blockDim.x;
+      for (long long i0 = u0 + threadIdx.x; i0 < u1; i0 += 2 * bs) {
+        float4 pv[2], qv[2], dv[2], ev[2], rv[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const long long i = i0 + j * bs;
+          if (i < u1) {
+            pv[j] = P4[i];
+            qv[j] = Q4[i];
+            dv[j] = D4[i];
+            ev[j] = E4[i];
+            rv[j] = R4[i];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const long long i = i0 + j * bs;
+          if (i >= u1) break;
+          float4 e4 = ev[j], r4 = rv[j];
+          e4.x += al * pv[j].x; e4.y += al * pv[j].y; e4.z += al * pv[j].z; e4.w += al * pv[j].w;
+          r4.x -= al * qv[j].x; r4.y -= al * qv[j].y; r4.z -= al * qv[j].z; r4.w -= al * qv[j].w;
+          const float4 z4 = make_float4(dv[j].x * r4.x, dv[j].y * r4.y, dv[j].z * r4.z, dv[j].w * r4.w);
+          E4[i] = e4;
+          R4[i] = r4;
+          Z4[i] = z4;
+          a3[0] += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
+          a3[1] += r4.x * z4.x + r4.y * z4.y + r4.z * z4.z + r4.w * z4.w;
+        }
+      }
+      for (long long i = (n4 << 2) + tid; i < nrow; i += gsz) {
+        e[i] += al * pnew[i];
+        const T ri = r[i] - al * q[i];
+        r[i] = ri;
+        const T zi = dinv[i] * ri;
+        z[i] = zi;
+        a3[0] += ri * ri;
+        a3[1] += ri * zi;
+      }
+    }
+    block_partials<2, T, T>(a3, A.partial, 3);
+    T t3[2];
+    if (!grid_barrier_total<2, T>(A.ctl, nb, A.partial, 3, t3)) return -1;
+    ++iters;
+    first = false;
+    const T rr = t3[0];
+    T rz_new = t3[1];
+    const bool reached = (double)rr * scale * scale <= target * target;
+    if (rr <= drop2 || reached || iters >= A.maxit) {
+      const int st = replace(rz_new);
+      if (st != 3) return st;
+    } else {
+      beta = rz_new / rz;
+    }
+    rz = rz_new;
+    T* t = pold;
+    pold = pnew;
+    pnew = t;
+  }
+}
+
 // y = S x for the operator of precision T (two grid-synchronised phases).
 template <class T>
 __device__ bool op_apply(const PcgArgs& A, const SysView<T>& s, const T* x, T* y) {
@@ -1146,8 +1336,16 @@ __global__ void __launch_bounds__(NT, 1) k_pcg(PcgArgs A) {
   const double bnorm = sqrt(grid_total(A.partial, 6));
   int iters = 0, status = 0, outer = 0;
   double rel = 0.0;
+  bool reliable = false;
+  if constexpr (sizeof(T) == 4 && !kQtt<TC>) reliable = A.reliable != 0;
   if (bnorm == 0.0) {
     status = 0;
+  } else if (reliable) {
+    if constexpr (sizeof(T) == 4 && !kQtt<TC>) {
+      const int st = pcg_reliable(A, pl, bnorm, iters, outer, rel);
+      if (st < 0) return;
+      status = st == 0 ? 0 : (st == 2 && iters == 0 ? 2 : 1);
+    }
   } else {
     for (outer = 0;; ++outer) {
       // r64 = rhs - S x
@@ -2429,6 +2627,7 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   A.qw0 = A.qw1 = nullptr;
   A.krylov = o->krylov == QP_BICGSTAB ? QP_BICGSTAB : QP_CG;
   A.direct = o->precond == QP_QTT_DIRECT ? 1 : 0;
+  A.reliable = (mixed && !use_qtt && A.krylov == QP_CG && !A.direct) ? 1 : 0;
   A.rec_cache = 0;
   A.xb = A.krylov == QP_BICGSTAB ? c->dm[12].ensure(5 * P * es) : nullptr;
   qp_dtype cdt = QP_F64;
@@ -2470,7 +2669,13 @@ static qp_solve_stats solve_once(qp_ctx* c, const double* rhs, double* dx, const
   // The fused kernel removes two of the three grid barriers of an iteration but
   // gathers border bodies redundantly and forms its operand on the fly; that
   // pays off while iterations are barrier-bound (few contacts per block).
-  const bool fused = !use_qtt && A.krylov == QP_CG && (c->Nc + c->num_sms - 1) / c->num_sms <= FUSED_MAX_CHUNK;
+  // Pipelined CG reaches a lower attainable accuracy than classic CG (its
+  // recurrences propagate local rounding errors; Cools et al., SIAM J. Matrix
+  // Anal. Appl. 39 (2018)): at FP64 tolerances below 1e-9 its recurrence
+  // residual drifts from the true one and the refinement restarts it, so those
+  // solves take the classic kernel.
+  const bool fused = !use_qtt && A.krylov == QP_CG && (c->Nc + c->num_sms - 1) / c->num_sms <= FUSED_MAX_CHUNK &&
+                     (mixed || o->tol >= 1e-9);
   if (fused) {
     solve_fused(c, rhs, dx, o, mixed);
     QP_CUDA(cudaMemcpyAsync(c->ctl_host, c->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));

@@ -57,16 +57,27 @@ class WarmStartNet:
         ctx.mpnn_warm_start(st, self.predict(ctx, Nc), self.out_scale, gn_min, shrink)
 
     def start(self, ctx: binding.Context, st: binding.State, Nc: int, gn_min: float, shrink: float = 0.9):
-        """PDIP start with the cold start as the fallback: the network's warm start
-        is kept when its dual residual is below the cold start's, else the cold
-        start is used.  Returns ("learned" or "cold", (eta, r_dual) of the cold
-        start, (eta, r_dual) of the learned start)."""
+        """Set the PDIP iterate to the network's warm start; returns (eta, r_dual) of
+        the cold start and of the learned start (for reporting)."""
         ctx.pdip_init(st, 1.0)
         cold = ctx.pdip_measure(st)
         self.warm_start(ctx, st, Nc, gn_min, shrink)
-        warm = ctx.pdip_measure(st)
-        if math.isfinite(warm[1]) and warm[1] < cold[1]:
-            return "learned", cold, warm
-        ctx.pdip_init(st, 1.0)
-        return "cold", cold, warm
+        return cold, ctx.pdip_measure(st)
 
+    def solve(self, ctx: binding.Context, st: binding.State, Nc: int, opts: binding.PdipOpts, gn_min: float,
+              cap: int, gap_tol: float = 1e-8, dual_tol: float = 1e-8, max_iter: int = 200, shrink: float = 0.9):
+        """PDIP to the tolerances from the learned start, with the cold start as the
+        fallback: when the PDIP from the learned start has not converged within
+        `cap` iterations, it is restarted from the cold start (Sec. 3.3 initial
+        point) with the full budget.  Neither the dual residual nor the objective
+        at the starting point predicts the PDIP's iteration count, so the fallback
+        is decided by the outcome.  Returns ("learned" or "cold", total PDIP
+        iterations, final PdipStats)."""
+        self.warm_start(ctx, st, Nc, gn_min, shrink)
+        stats, n = ctx.pdip_solve(st, opts, gap_tol=gap_tol, dual_tol=dual_tol, max_iter=cap,
+                                  allow=(binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL))
+        if stats.status == binding.QP_OK:
+            return "learned", n, stats
+        ctx.pdip_init(st, 1.0)
+        stats2, n2 = ctx.pdip_solve(st, opts, gap_tol=gap_tol, dual_tol=dual_tol, max_iter=max_iter)
+        return "cold", n + n2, stats2

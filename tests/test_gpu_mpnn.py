@@ -73,9 +73,14 @@ def test_adam_step(ctx):
     m1 = 0.9 * m0 + 0.1 * gg
     v1 = 0.999 * v0 + 0.001 * gg * gg
     p1 = p0 - 1e-2 * (m1 / (1 - 0.9 ** 3)) / (np.sqrt(v1 / (1 - 0.999 ** 3)) + 1e-8)
-    # the update itself, entry by entry: the FP32 bias correction 1 - beta2^3 cancels to
-    # about 2e-5 relative, so the step is checked to 1e-4 of max(|dp_i|, 1e-3 max|dp|)
-    assert_close(to_np(params).astype(np.float64) - p0, p1 - p0, 1e-4, floor_rel=1e-3, what="Adam update")
+    # entry by entry: the FP32 bias correction 1 - beta2^3 cancels to about 2e-5
+    # relative, so the step dp is held to 1e-4 of max(|dp_i|, 1e-3 max|dp|); the
+    # parameter is stored in FP32, which adds one rounding of |p1| (2^-24 |p1|)
+    got = to_np(params).astype(np.float64)
+    dp = np.abs(p1 - p0)
+    bound = 1e-4 * np.maximum(dp, 1e-3 * dp.max()) + 2.0 ** -23 * np.abs(p1)
+    err = np.abs(got - p1)
+    assert np.all(err <= bound), (int(np.argmax(err / bound)), float((err / bound).max()))
 
 
 def test_warm_start_matches_oracle(ctx):
@@ -106,19 +111,72 @@ def test_training_fits_pdip_iterates(ctx):
     assert max(last) <= 0.2 * min(first)
 
 
-def test_start_never_worse_than_cold(ctx):
-    """net.start keeps the learned start only when its dual residual is below the
-    cold start's; an untrained network falls back to the cold start exactly."""
-    pb = Problem(ctx, scene_for("pile8", 1))
-    g = torch.zeros(pb.P, dtype=torch.float64, device="cuda")
-    lam = torch.zeros(2 * pb.Nc, dtype=torch.float64, device="cuda")
-    st = pb.ctx.state(g, lam)
-    pb.ctx.pdip_init(st, 1.0)
-    _, rd_cold = pb.ctx.pdip_measure(st)
-    g0 = g.clone()
-    net = learned.WarmStartNet(3, SCALE, out_scale=1e4)  # wildly scaled: far from the cold start
-    used, cold, warm = net.start(pb.ctx, st, pb.Nc, gn_min=1.0)
-    _, rd = pb.ctx.pdip_measure(st)
-    assert rd <= rd_cold and cold[1] == rd_cold
-    if used == "cold":
-        assert torch.equal(g, g0)
+COL_SCALE = [1.0, 1.0, 1.0, 0.05, 0.05, 0.05, 0.05, 2.0]
+
+
+def column_system(seed):
+    """A 16 x 16 x 10 column scene in its own context, PDIP state at the cold start."""
+    from paper_1808_02558_gb300 import workload
+
+    sc = scene_for("stack16", seed)
+    c = binding.Context()
+    _, con = workload.assemble(c, sc)
+    g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+    st = c.state(g, lam)
+    rows = (3 * torch.arange(con.Nc, device="cuda")[:, None] + torch.arange(3, device="cuda")[None, :]).reshape(-1)
+    return c, con, g, lam, st, rows
+
+
+def cold_solve(c, st):
+    opts = c.pdip_opts(c.solve_opts(tol=1e-10, maxit=200000))
+    c.pdip_init(st, 1.0)
+    stats, n = c.pdip_solve(st, opts, gap_tol=1e-8, dual_tol=1e-8, max_iter=200)
+    assert stats.status == binding.QP_OK
+    return opts, n
+
+
+def test_learned_start_cuts_pdip_iterations(ctx):
+    """The network, trained on converged PDIP solutions that the library itself
+    computes for columns of seeds 2-9, starts the PDIP of the unseen seed 1: it
+    converges (gap and dual residual 1e-8) in fewer iterations than the cold
+    start, to the same impulses (1e-6 per entry)."""
+    train, cold_its = [], []
+    for seed in range(2, 10):
+        c, con, g, lam, st, rows = column_system(seed)
+        _, n = cold_solve(c, st)
+        cold_its.append(n)
+        train.append((c, g[rows].clone()))
+    out_scale = float(torch.cat([t[0::3] for _, t in train]).mean())
+    net = learned.WarmStartNet(11, COL_SCALE, out_scale)
+    first = net.train_step(train[0][0], train[0][1], 1e-3)
+    for _ in range(300):
+        for c, t in train:
+            last = net.train_step(c, t, 1e-3)
+    assert last <= 0.01 * first
+    c, con, g, lam, st, rows = column_system(1)
+    opts, n_cold = cold_solve(c, st)
+    g_cold = g[rows].cpu().numpy()
+    used, n_learned, stats = net.solve(c, st, con.Nc, opts, gn_min=1e-3 * out_scale, cap=max(cold_its))
+    print(f"PDIP iterations: cold {n_cold}, learned start {n_learned} ({used})")
+    assert used == "learned" and stats.status == binding.QP_OK
+    assert n_learned < n_cold
+    assert_close(g[rows].cpu().numpy(), g_cold, 1e-6, what="impulses from the learned start")
+    for c_, _ in train:
+        c_.close()
+    c.close()
+
+
+def test_learned_start_falls_back_to_cold(ctx):
+    """An untrained, wildly scaled network: the PDIP from its start does not
+    converge within the cap, the solve restarts from the cold start and ends at
+    the cold start's solution."""
+    c, con, g, lam, st, rows = column_system(1)
+    opts, n_cold = cold_solve(c, st)
+    g_cold = g[rows].cpu().numpy()
+    net = learned.WarmStartNet(3, COL_SCALE, out_scale=1e6)
+    used, n, stats = net.solve(c, st, con.Nc, opts, gn_min=1.0, cap=3)
+    assert used == "cold" and stats.status == binding.QP_OK
+    assert n == 3 + n_cold
+    assert_close(g[rows].cpu().numpy(), g_cold, 1e-6, what="impulses after the fallback")
+    c.close()
