@@ -161,7 +161,7 @@ STATUS_NAMES = {0: "ok", -4: "not_converged", -5: "breakdown", -6: "linesearch_f
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pcg<float, void>
 # launch of the 40^3 window, from an ncu capture of this kernel version (caches
 # flushed by ncu before the launch).  Reset to None when the kernel changes.
-KPCG_DRAM_BYTES_PER_LAUNCH = 184.56e6
+KPCG_DRAM_BYTES_PER_LAUNCH = None  # recaptured after the reliable-update change
 
 
 # FP32 CUDA-core peak of the part from its unit counts: 152 SMs x 128 FP32 lanes x
@@ -409,6 +409,8 @@ def run_ours(args):
     ts_out = time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream) if args.ts_steps > 0 else None
     batch_out = batched_leg(args, binding, workload) if args.batch_scenes > 0 else None
     learned_out = learned_leg(args, binding, workload) if args.learned_steps > 0 else None
+    if learned_out is not None:
+        learned_out["network_at_bench_scale"] = mpnn_scale_leg(binding, workload, scene, flush, stream)
     configs_out = None
     if args.config_legs:
         cpu_ok = rank == 0 and not args.no_cpu_baseline
@@ -470,17 +472,19 @@ FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (nominal; no measured figure)
 
 
 def n_apply_leg(binding, ctx, st, Nc, M, P, flush, stream, reps=20):
-    """The standalone operator apply y = S x (newton_apply) on the bench's scene,
-    FP64 and FP32, with and without the PDIP blocks, L2 flushed before every
-    timed call.  Algorithmic bytes, FP64 (FP32 halves the values): per contact
-    x 24 + y 24 + frame (n, t1) 48 + arms 48 + ids 8 = 152 B, plus, with the
-    state, gamma 24 + lambda 16 read and H 48 written and read (136 B); per body
-    1/m, 1/I 16 + w written 48 + read 48 = 112 B.  Pad rows are excluded.
-    Flops: 33 per incidence (two per contact), 47 per contact in the contact pass
-    (65 with H), 6 per body, and 27 per contact for the Schur blocks.  The bound
-    is HBM when flop/byte is below the ridge of the dtype's ALU peak over the
-    measured HBM peak (FP32: 80.5 TFLOP/s derived; FP64: 1.25 TFLOP/s nominal),
-    else that ALU peak."""
+    """The standalone operator apply y = S x (newton_apply, one fused launch) on
+    the bench's scene, FP64 and FP32, with and without the PDIP state, L2 flushed
+    before every timed call.  Algorithmic bytes (vb = 8 or 4 bytes per value):
+    per contact x 3 vb + y 3 vb + frame 6 vb (n and t1; t2 = n x t1) + arms 6 vb
+    = 18 vb, ids 8 B and incidence codes 8 B; with the state, gamma 24 B and
+    lambda 16 B (FP64; the 3x3 block is formed in registers, never stored); per
+    body 1/m and 1/I 2 vb and its CSR offset 4 B (the body intermediate stays in
+    shared memory).  Pad
+    rows are excluded.  Flops: 33 per incidence (two per contact), 47 per contact
+    in the contact pass, 6 per body, and 45 per contact for forming and applying
+    the block.  The bound is HBM when flop/byte is below the ridge of the dtype's
+    ALU peak over the measured HBM peak (FP32: 80.5 TFLOP/s derived; FP64: 1.25
+    TFLOP/s nominal), else that ALU peak."""
     import torch
 
     hbm, src = peaks()
@@ -505,9 +509,11 @@ def n_apply_leg(binding, ctx, st, Nc, M, P, flush, stream, reps=20):
                 e1.record(stream)
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
-            per_c = 18 * vb + 8 + ((5 + 12) * vb if with_state else 0)
-            nbytes = Nc * per_c + M * 14 * vb
-            flops = Nc * (2 * 33 + (65 + 27 if with_state else 47)) + M * 6
+            per_c = 18 * vb + 16 + (40 if with_state else 0)
+            # FP32: one launch, w stays in shared memory; FP64: two launches, w (6 values
+            # per body) is written by the gather and read back by the contact pass
+            nbytes = Nc * per_c + M * (2 * vb + 4 + (12 * vb if vb == 8 else 0))
+            flops = Nc * (2 * 33 + 47 + (45 if with_state else 0)) + M * 6
             t = statistics.median(ms) / 1e3
             if flops / nbytes < alu * 1e12 / (hbm * 1e9):
                 roof = {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": hbm, "unit": "GB/s",
@@ -516,10 +522,11 @@ def n_apply_leg(binding, ctx, st, Nc, M, P, flush, stream, reps=20):
                 roof = {"bound": "alu", "achieved": flops / t / 1e12, "peak": alu, "unit": "TFLOP/s",
                         "frac": flops / t / 1e12 / alu, "peak_source": alu_src}
             key = name + ("_with_state" if with_state else "")
-            out[key] = {"us": t * 1e6, "bytes": nbytes, "flops": flops, "launches": 3 if with_state else 2,
+            out[key] = {"us": t * 1e6, "bytes": nbytes, "flops": flops, "launches": 2 if vb == 8 else 1,
                         "gbs": nbytes / t / 1e9, "roofline": roof}
-    out["note"] = ("median of %d calls, L2 flushed before each; with_state includes the Schur-block "
-                   "build from (gamma, lambda)" % reps)
+    out["note"] = ("median of %d calls, L2 flushed before each; FP32 one fused launch, FP64 two (body "
+                   "gather, contact pass); with_state forms each contact's Schur block from (gamma, lambda) in "
+                   "registers" % reps)
     return out
 
 
@@ -734,6 +741,51 @@ def learned_leg(args, binding, workload):
             "eval": evals,
             "iters_saved_mean": statistics.mean(e["cold_iters"] - e["learned_iters"] for e in evals),
             "speedup_mean": statistics.mean(e["cold_ms"] / e["learned_ms"] for e in evals)}
+
+
+def mpnn_scale_leg(binding, workload, scene, flush, stream, reps=10):
+    """The warm-start network on the bench's scene (the 40^3 pile, 191 806
+    contacts): one forward pass and one gradient (forward + backward), device
+    time with the L2 flushed before each call.  The three hidden layers are
+    Nc x 128 by 128 x 64 products on the tensor cores (tcgen05, split TF32), the
+    backward's input gradients Nc x 64 by 64 x 128 likewise; flops counted are
+    those of the dense layers (2 Nc K J per product)."""
+    import torch
+
+    from paper_1808_02558_gb300 import learned
+
+    ctx = binding.Context()
+    _, con = workload.assemble(ctx, scene)
+    Nc = con.Nc
+    params = learned.init_params(5)
+    scale = [1.0, 1.0, 1.0, 0.05, 5.0, 5.0, 5.0, 2.0]
+    out = torch.empty(3 * Nc, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(params)
+    target = torch.randn(3 * Nc, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    f_ms = timed(lambda: ctx.mpnn_forward(params, scale, out))
+    g_ms = timed(lambda: ctx.mpnn_grad(params, scale, target, grad))
+    dense_f = 2 * Nc * (8 * 64 + 3 * 128 * 64 + 64 * 3)
+    dense_g = dense_f + 2 * Nc * (3 * 2 * 128 * 64 + 64 * 8 + 2 * 64 * 3)
+    ctx.close()
+    return {"contacts": Nc, "forward_ms": f_ms, "grad_ms": g_ms, "forward_dense_flops": dense_f,
+            "grad_dense_flops": dense_g, "forward_tflops": dense_f / f_ms / 1e9, "grad_tflops": dense_g / g_ms / 1e9,
+            "note": "median of %d calls each, L2 flushed before each; times include the message passing, "
+                    "the small input/output layers and (grad) the loss read-back" % reps}
 
 
 def batched_leg(args, binding, workload):

@@ -599,6 +599,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   QP_CUDA(cudaStreamSynchronize(st));
   c->have_contacts = true;
   c->part_G = 0;  // the Krylov partition follows the contact set
+  c->apart_G = 0;  // and so does the fused apply's
 
   out->M = M;
   out->Nc = Nc;

@@ -102,6 +102,9 @@ struct qp_ctx {
   // contact partition of the fused Krylov kernel (one contiguous chunk per block)
   int part_G = 0, part_chunk = 0, part_maxb = 0, part_nbmax = 0;
   qp::Buf part_nb, part_bodies, part_cl;
+  // contact partition of the standalone fused apply (newton_apply)
+  int apart_G = 0, apart_chunk = 0, apart_maxb = 0, apart_nbmax = 0;
+  qp::Buf apart_nb, apart_bodies, apart_cl;
   qp::Buf fused_pool;
   qp::Buf mp_act, mp_w, mp_grad, mp_sum;  // learned warm start: activations, BF16 weights, scratch
   qp::Buf batch64, batch32, batch_table;  // batched solves: per-scene vectors; table (first context)  // records of the fused pipelined solver (never shared with the classic solver)

@@ -7,8 +7,13 @@
 // relative velocity in the contact frame, mu).  Parameters are BF16-rounded
 // for the passes (FP32 master kept by the caller), activations and sums FP32.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace qp {
 namespace {
@@ -132,27 +137,6 @@ __global__ void k_mp_dense_bwd_x(int Nc, const float* __restrict__ dZ, int J, co
   }
 }
 
-// gW[j][k] = sum_c dZ[c][j] X[c][k] (X = [Xa, Xb]); gb[j] = sum_c dZ[c][j]
-__global__ void k_mp_dense_bwd_w(int Nc, const float* __restrict__ dZ, int J, const float* __restrict__ Xa, int Ka,
-                                 const float* __restrict__ Xb, int Kb, float* __restrict__ gW, float* __restrict__ gb) {
-  const int K = Ka + Kb;
-  const int n = J * (K + 1);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int j = i / (K + 1), k = i - j * (K + 1);
-    double s = 0.0;  // FP64: one long sum per weight, exact enough for the oracle comparison
-    if (k == K) {
-      for (int c = 0; c < Nc; ++c) s += dZ[(size_t)c * J + j];
-      gb[j] = (float)s;
-    } else {
-      for (int c = 0; c < Nc; ++c) {
-        const float x = k < Ka ? Xa[(size_t)c * Ka + k] : Xb[(size_t)c * Kb + (k - Ka)];
-        s += (double)(dZ[(size_t)c * J + j] * x);
-      }
-      gW[j * K + k] = (float)s;
-    }
-  }
-}
-
 __global__ void k_mp_adam(int n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                           const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1, float c2) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -190,10 +174,302 @@ __global__ void k_mp_warm(int Nc, int slots, long long P, const float* __restric
   }
 }
 
+// ---------------------------------------------------------------- tensor-core rows GEMM
+// OUT[r][n] = sum_k A[r][k] B[n][k] on the tensor cores (tcgen05, kind::tf32),
+// 128 rows per tile, persistent blocks of 128 threads.  A is FP32, read by TMA
+// from up to two row-major sources of 64 columns (kb0 blocks of 32 columns from
+// the first, the rest from the second: the concatenation [h; s] of a layer);
+// B comes from the BF16 weights, staged once per block as FP32 (exact in TF32).
+// Products are FP32-accurate: A = A_hi + A_lo, A_hi = A with its 13 low mantissa
+// bits cleared (exact in TF32), A_lo = A - A_hi (exact in FP32, within 2^-11 of
+// its own size after the MMA's TF32 conversion), two MMAs per K step, so the
+// error is about 2^-21 |A| |B| per term.  The accumulator (128 lanes x N FP32
+// columns) lives in tensor memory; each warp reads its 32 rows back.
+// EPI 0: Y0[r][n] = relu(acc + bias[n]) (N = 64).  EPI 1: Y0[r][n] = acc for
+// n < 64, Y1[r][n - 64] = acc for n >= 64 (N = 128).
+constexpr long long TC_BUDGET = 2000000000LL;  // clock ticks (~1 s) per wait
+
+template <int N, int KB, int EPI>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_rows(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1, int kb0, int rows,
+              const __nv_bfloat16* __restrict__ W, int ldw, int wtrans, const __nv_bfloat16* __restrict__ bias,
+              float* __restrict__ Y0, float* __restrict__ Y1, int* __restrict__ err) {
+  using namespace tc;
+  constexpr int A_BLK = 128 * 128;  // bytes of a 128-row x 32-column block
+  constexpr int B_BLK = N * 128;
+  constexpr int A_BYTES = KB * A_BLK, B_BYTES = KB * B_BLK;
+  // shared memory: B, two A stages (the next tile's copy overlaps this tile's work), A_lo
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  unsigned char* base = tc_raw + ((1024u - (smem_addr(tc_raw) & 1023u)) & 1023u);
+  unsigned char* sB = base;
+  unsigned char* const sA0 = base + B_BYTES;  // stage s at sA0 + s A_BYTES
+  unsigned char* sL = base + B_BYTES + 2 * A_BYTES;
+  __shared__ uint64_t bar_tma[2], bar_mma;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (rows + 127) / 128;
+  auto issue = [&](int t, int st) {  // thread 0: the A tile of row block t into stage st
+    mbar_arrive_expect_tx(&bar_tma[st], A_BYTES);
+    for (int j = 0; j < KB; ++j) {
+      if (j < kb0) tma_load_2d(sA0 + st * A_BYTES + j * A_BLK, &mA0, &bar_tma[st], 32 * j, t * 128);
+      else tma_load_2d(sA0 + st * A_BYTES + j * A_BLK, &mA1, &bar_tma[st], 32 * (j - kb0), t * 128);
+    }
+  };
+  if (tid == 0) {
+    mbar_init(&bar_tma[0], 1);
+    mbar_init(&bar_tma[1], 1);
+    mbar_init(&bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, N);
+    tmem_relinquish();
+  }
+  // B(n, k) = W[n ldw + k] (or W[k ldw + n]) into the swizzled K-major layout
+  for (int i = tid; i < N * KB * 32; i += blockDim.x) {
+    const int n = i / (KB * 32), k = i - n * (KB * 32);
+    const float w = __bfloat162float(wtrans ? W[(size_t)k * ldw + n] : W[(size_t)n * ldw + k]);
+    const int kk = k & 31;
+    *reinterpret_cast<float*>(sB + (k >> 5) * B_BLK + n * 128 + (((kk >> 2) ^ (n & 7)) << 4) + ((kk & 3) << 2)) = w;
+  }
+  fence_async_shared();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = idesc_tf32(128, N);
+  uint32_t ph_tma = 0u, ph_mma = 0u;  // bit s: parity of stage s's next phase
+  int fail = 0;      // 1: a wait expired
+  int inflight = 0;  // stages with a copy issued and not yet waited for (bit mask)
+  if ((int)blockIdx.x < ntiles) inflight = 1;
+  int st = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, st ^= 1) {
+    const int r0 = t * 128;
+    if (!mbar_wait(&bar_tma[st], (ph_tma >> st) & 1u, TC_BUDGET)) fail = 1;
+    if (__syncthreads_or(fail)) {
+      fail = 1;
+      break;
+    }
+    ph_tma ^= 1u << st;
+    inflight &= ~(1 << st);
+    // the other stage is free (its tile's MMAs completed): start the next copy now
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      if (tid == 0) issue(tn, st ^ 1);
+      inflight |= 1 << (st ^ 1);
+    }
+    // A_hi in place, A_lo beside it (same swizzled positions)
+    float4* a4 = reinterpret_cast<float4*>(sA0 + st * A_BYTES);
+    float4* l4 = reinterpret_cast<float4*>(sL);
+    for (int i = tid; i < A_BYTES / 16; i += blockDim.x) {
+      const float4 a = a4[i];
+      float4 h;
+      h.x = __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u);
+      h.y = __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u);
+      h.z = __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u);
+      h.w = __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u);
+      a4[i] = h;
+      l4[i] = make_float4(a.x - h.x, a.y - h.y, a.z - h.z, a.w - h.w);
+    }
+    fence_async_shared();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      const uint32_t ah = smem_addr(sA0 + st * A_BYTES), al = smem_addr(sL), bb = smem_addr(sB);
+      for (int kk = 0; kk < 4 * KB; ++kk) {
+        const uint32_t ao = (kk >> 2) * A_BLK + (kk & 3) * 32, bo = (kk >> 2) * B_BLK + (kk & 3) * 32;
+        const uint64_t bd = desc_k_sw128(bb + bo);
+        mma_tf32(tmem, desc_k_sw128(ah + ao), bd, idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(tmem, desc_k_sw128(al + ao), bd, idesc, 1u);
+      }
+      mma_commit(&bar_mma);
+    }
+    if (!mbar_wait(&bar_mma, ph_mma, TC_BUDGET)) fail = 1;
+    if (__syncthreads_or(fail)) {
+      fail = 1;
+      break;
+    }
+    ph_mma ^= 1u;
+    fence_after_sync();
+    const int r = r0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      float v[32];
+      tmem_ld32(tl + (uint32_t)c0, v);
+      if (r < rows) {
+        if constexpr (EPI == 0) {
+          float4* o = reinterpret_cast<float4*>(Y0 + (size_t)r * 64 + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float4 w;
+            w.x = fmaxf(v[4 * q] + __bfloat162float(bias[c0 + 4 * q]), 0.f);
+            w.y = fmaxf(v[4 * q + 1] + __bfloat162float(bias[c0 + 4 * q + 1]), 0.f);
+            w.z = fmaxf(v[4 * q + 2] + __bfloat162float(bias[c0 + 4 * q + 2]), 0.f);
+            w.w = fmaxf(v[4 * q + 3] + __bfloat162float(bias[c0 + 4 * q + 3]), 0.f);
+            o[q] = w;
+          }
+        } else {
+          float* dst = c0 < 64 ? Y0 + (size_t)r * 64 + c0 : Y1 + (size_t)r * 64 + (c0 - 64);
+          float4* o = reinterpret_cast<float4*>(dst);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+  }
+  if (fail) {
+    // let copies and MMAs of the failed step finish (bounded) before the
+    // block's shared and tensor memory go away
+    for (int k = 0; k < 2; ++k)
+      if (inflight & (1 << k)) mbar_wait(&bar_tma[k], (ph_tma >> k) & 1u, TC_BUDGET);
+    mbar_wait(&bar_mma, ph_mma, TC_BUDGET);
+    if (tid == 0) atomicExch(err, 1);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0) tmem_dealloc(tmem, N);
+}
+
+// Weight gradient in two deterministic passes: block g sums its chunk of rows,
+// part[g][j (K + 1) + k] = sum_c dZ[c][j] X[c][k] (k < K) and sum_c dZ[c][j]
+// (k = K), staging 32 rows of dZ and X = [Xa, Xb] in shared memory at a time;
+// then the partials are added in block order in FP64.
+template <int J, int K, int PER>
+__global__ void __launch_bounds__(256) k_wgrad_part(int Nc, int chunk, const float* __restrict__ dZ,
+                                                    const float* __restrict__ Xa, int Ka, const float* __restrict__ Xb,
+                                                    float* __restrict__ part) {
+  static_assert(PER * 256 >= J * (K + 1), "outputs per thread");
+  __shared__ float sz[32][J];
+  __shared__ float sx[32][K + 1];
+  const int c0 = blockIdx.x * chunk, c1 = min(Nc, c0 + chunk);
+  float acc[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) acc[i] = 0.f;
+  for (int r0 = c0; r0 < c1; r0 += 32) {
+    const int nr = min(32, c1 - r0);
+    for (int i = threadIdx.x; i < 32 * J; i += blockDim.x) {
+      const int r = i / J, j = i - r * J;
+      sz[r][j] = r < nr ? dZ[(size_t)(r0 + r) * J + j] : 0.f;
+    }
+    for (int i = threadIdx.x; i < 32 * K; i += blockDim.x) {
+      const int r = i / K, k = i - r * K;
+      float x = 0.f;
+      if (r < nr) x = k < Ka ? Xa[(size_t)(r0 + r) * Ka + k] : Xb[(size_t)(r0 + r) * (K - Ka) + (k - Ka)];
+      sx[r][k] = x;
+    }
+    for (int r = threadIdx.x; r < 32; r += blockDim.x) sx[r][K] = 1.f;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int o = threadIdx.x + i * 256;
+      if (o < J * (K + 1)) {
+        const int j = o / (K + 1), k = o - j * (K + 1);
+        float s = acc[i];
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) s = fmaf(sz[r][j], sx[r][k], s);
+        acc[i] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int o = threadIdx.x + i * 256;
+    if (o < J * (K + 1)) part[(size_t)blockIdx.x * J * (K + 1) + o] = acc[i];
+  }
+}
+
+// gW[j K + k] = sum_g part[g][j (K+1) + k], gb[j] = sum_g part[g][j (K+1) + K]
+__global__ void k_wgrad_sum(int nparts, int J, int K, const float* __restrict__ part, float* __restrict__ gW,
+                            float* __restrict__ gb) {
+  const int n = J * (K + 1);
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < nparts; ++g) s += (double)part[(size_t)g * n + o];
+    const int j = o / (K + 1), k = o - j * (K + 1);
+    if (k == K) gb[j] = (float)s;
+    else gW[j * K + k] = (float)s;
+  }
+}
+
 inline int blocks_for(long long n, int per = 256, int cap = 152 * 32) {
   long long b = (n + per - 1) / per;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
+}
+
+// ---- host side of the tensor-core GEMM
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  QP_REQUIRE(fn != nullptr, QP_CUDA_ERROR, "cuTensorMapEncodeTiled is not available");
+  return fn;
+}
+
+// Row-major FP32 matrix [rows][64], boxes of 128 rows x 32 columns (128 bytes
+// wide, the 128-byte swizzle); rows past the end read as zeros.
+CUtensorMap rows64_map(const float* base, int rows) {
+  QP_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15u) == 0, QP_CUDA_ERROR, "tensor map base not 16-byte aligned");
+  CUtensorMap m;
+  const cuuint64_t gdim[2] = {64, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {64 * sizeof(float)};
+  const cuuint32_t box[2] = {32, 128};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = tmap_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride,
+                                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  QP_REQUIRE(r == CUDA_SUCCESS, QP_CUDA_ERROR, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+int* tc_flag(qp_ctx* c) {
+  char* p = static_cast<char*>(c->mp_sum.ensure(64));
+  return reinterpret_cast<int*>(p + 32);
+}
+
+template <int N, int KB, int EPI>
+void launch_tc_rows(qp_ctx* c, const float* A0, const float* A1, int kb0, int rows, const __nv_bfloat16* W, int ldw,
+                    int wtrans, const __nv_bfloat16* bias, float* Y0, float* Y1) {
+  if (rows <= 0) return;
+  const CUtensorMap m0 = rows64_map(A0, rows);
+  const CUtensorMap m1 = rows64_map(A1 ? A1 : A0, rows);
+  auto k = k_tc_rows<N, KB, EPI>;
+  const int smem = KB * N * 128 + 3 * KB * 128 * 128 + 1024;  // B, two A stages, A_lo, alignment
+  QP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int grid = std::min((rows + 127) / 128, c->num_sms);
+  k<<<grid, 128, smem, c->stream>>>(m0, m1, kb0, rows, W, ldw, wtrans, bias, Y0, Y1, tc_flag(c));
+  QP_CUDA(cudaGetLastError());
+}
+
+// Weight and bias gradient of a dense layer (dZ [Nc][J], X = [Xa (Ka) | Xb (K - Ka)]).
+template <int J, int K>
+void launch_wgrad(qp_ctx* c, const float* dZ, const float* Xa, int Ka, const float* Xb, float* part, float* gW,
+                  float* gb) {
+  constexpr int PER = (J * (K + 1) + 255) / 256;
+  const int Nc = c->Nc, chunk = 256;
+  const int nparts = (Nc + chunk - 1) / chunk;
+  k_wgrad_part<J, K, PER><<<nparts, 256, 0, c->stream>>>(Nc, chunk, dZ, Xa, Ka, Xb, part);
+  k_wgrad_sum<<<(J * (K + 1) + 255) / 256, 256, 0, c->stream>>>(nparts, J, K, part, gW, gb);
+  QP_CUDA(cudaGetLastError());
+}
+
+void check_tc_flag(qp_ctx* c) {
+  int h = 0;
+  QP_CUDA(cudaMemcpyAsync(&h, tc_flag(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  QP_CUDA(cudaStreamSynchronize(c->stream));
+  QP_REQUIRE(h == 0, QP_TIMEOUT, "tensor-core GEMM: a wait expired");
 }
 
 struct Net {
@@ -224,6 +500,7 @@ Net workspace(qp_ctx* c) {
 
 void forward(qp_ctx* c, const float* params, const float* scale_host, float* out, Net& n) {
   cudaStream_t st = c->stream;
+  QP_CUDA(cudaMemsetAsync(tc_flag(c), 0, sizeof(int), st));
   const int Nc = c->Nc, M = c->M;
   k_mp_round<<<blocks_for(NPAR), 256, 0, st>>>(params, n.pw, NPAR);
   Scale sc;
@@ -238,8 +515,8 @@ void forward(qp_ctx* c, const float* params, const float* scale_host, float* out
       k_mp_gather<<<blocks_for((long long)Nc * MW), 256, 0, st>>>(Nc, M, c->ca.as<int>(), c->cb.as<int>(), n.Mb,
                                                                  n.S[l], 0);
       const __nv_bfloat16* W = n.pw + OFF_L + l * LAYER;
-      k_mp_dense<<<blocks_for((long long)Nc * MW), 256, 0, st>>>(Nc, n.H[l], MW, n.S[l], MW, W, W + MW * 2 * MW, MW, 1,
-                                                                n.H[l + 1]);
+      // H[l+1] = relu(W [H[l]; S[l]] + b): Nc x 128 by 128 x 64 on the tensor cores
+      launch_tc_rows<MW, 4, 0>(c, n.H[l], n.S[l], 2, Nc, W, 2 * MW, 0, W + MW * 2 * MW, n.H[l + 1], nullptr);
     }
     k_mp_dense<<<blocks_for((long long)Nc * MO), 256, 0, st>>>(Nc, n.H[ML], MW, nullptr, 0, n.pw + OFF_WO,
                                                               n.pw + OFF_BO, MO, 0, out);
@@ -272,6 +549,7 @@ int mpnn_forward(qp_ctx_t c, const float* params, const float* feat_scale, float
   QP_REQUIRE(params && feat_scale && (out || c->Nc == 0), QP_INVALID_ARG, "mpnn_forward: null argument");
   Net n = workspace(c);
   forward(c, params, feat_scale, out, n);
+  check_tc_flag(c);
   MP_END(c)
 }
 
@@ -287,30 +565,36 @@ int mpnn_grad(qp_ctx_t c, const float* params, const float* feat_scale, const fl
   cudaStream_t st = c->stream;
   forward(c, params, feat_scale, n.O, n);
   // scratch: per-entry errors (double) [3Nc], dO [3Nc], three [Nc][64] buffers
-  const size_t nb = (size_t)3 * Nc * sizeof(double) + (size_t)3 * Nc * sizeof(float) + 3 * (size_t)Nc * MW * 4 + 256;
+  // (every buffer starts on a 256-byte boundary: the tensor-core GEMM reads A by TMA)
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nparts = ((size_t)Nc + 255) / 256;
+  const size_t o_dO = up((size_t)3 * Nc * sizeof(double)), o_A = o_dO + up((size_t)3 * Nc * sizeof(float));
+  const size_t o_B = o_A + up((size_t)Nc * MW * 4), o_C = o_B + up((size_t)Nc * MW * 4);
+  const size_t o_P = o_C + up((size_t)Nc * MW * 4);
+  const size_t nb = o_P + nparts * MW * (2 * MW + 1) * sizeof(float);
   char* s = static_cast<char*>(c->mp_grad.ensure(nb));
   double* err = reinterpret_cast<double*>(s);
-  float* dO = reinterpret_cast<float*>(err + 3 * (size_t)Nc);
-  float* A = dO + 3 * (size_t)Nc + 4;
-  float* B = A + (size_t)Nc * MW;
-  float* Cs = B + (size_t)Nc * MW;
+  float* dO = reinterpret_cast<float*>(s + o_dO);
+  float* A = reinterpret_cast<float*>(s + o_A);
+  float* B = reinterpret_cast<float*>(s + o_B);
+  float* Cs = reinterpret_cast<float*>(s + o_C);
+  float* part = reinterpret_cast<float*>(s + o_P);
   float* dM = n.Mb;  // the forward pass is done with it
-  double* lsum = static_cast<double*>(c->mp_sum.ensure(sizeof(double)));
+  double* lsum = static_cast<double*>(c->mp_sum.ensure(64));  // the GEMM flag shares this buffer
   const long long nh = (long long)Nc * MW;
   k_mp_loss<<<blocks_for(3LL * Nc), 256, 0, st>>>(3 * Nc, n.O, target, dO, err);
   k_mp_sum<<<1, 256, 0, st>>>(3 * Nc, err, lsum);
   // head: o = Wo h3 + bo
-  k_mp_dense_bwd_w<<<blocks_for(MO * (MW + 1)), 256, 0, st>>>(Nc, dO, MO, n.H[ML], MW, nullptr, 0, grad + OFF_WO,
-                                                             grad + OFF_BO);
+  launch_wgrad<MO, MW>(c, dO, n.H[ML], MW, nullptr, part, grad + OFF_WO, grad + OFF_BO);
   k_mp_dense_bwd_x<<<blocks_for(nh), 256, 0, st>>>(Nc, dO, MO, n.pw + OFF_WO, MW, 0, A, nullptr);
   for (int l = ML - 1; l >= 0; --l) {
     // layer l: H[l+1] = relu(W [H[l]; S[l]] + b); A holds d/dH[l+1]
     const __nv_bfloat16* W = n.pw + OFF_L + l * LAYER;
     float* gW = grad + OFF_L + l * LAYER;
     k_mp_relu_bwd<<<blocks_for(nh), 256, 0, st>>>(nh, n.H[l + 1], A);
-    k_mp_dense_bwd_w<<<blocks_for(MW * (2 * MW + 1)), 256, 0, st>>>(Nc, A, MW, n.H[l], MW, n.S[l], MW, gW,
-                                                                    gW + MW * 2 * MW);
-    k_mp_dense_bwd_x<<<blocks_for((long long)Nc * 2 * MW), 256, 0, st>>>(Nc, A, MW, W, MW, MW, B, Cs);
+    launch_wgrad<MW, 2 * MW>(c, A, n.H[l], MW, n.S[l], part, gW, gW + MW * 2 * MW);
+    // [dH[l], dS[l]] = dZ W: Nc x 64 by 64 x 128 on the tensor cores (B(n, j) = W[j][n])
+    launch_tc_rows<2 * MW, 2, 1>(c, A, nullptr, 2, Nc, W, 2 * MW, 1, nullptr, B, Cs);
     // S[l] = gather(bodysum(H[l])): its adjoint is the same pair of sums
     k_mp_bodysum<<<blocks_for((long long)M * MW), 256, 0, st>>>(M, c->bptr.as<int>(), c->inc.as<int>(), Cs, dM);
     k_mp_gather<<<blocks_for(nh), 256, 0, st>>>(Nc, M, c->ca.as<int>(), c->cb.as<int>(), dM, B, 1);
@@ -320,9 +604,9 @@ int mpnn_grad(qp_ctx_t c, const float* params, const float* feat_scale, const fl
   }
   // input layer: H[0] = relu(W0 X0 + b0)
   k_mp_relu_bwd<<<blocks_for(nh), 256, 0, st>>>(nh, n.H[0], A);
-  k_mp_dense_bwd_w<<<blocks_for(MW * (MF + 1)), 256, 0, st>>>(Nc, A, MW, n.X0, MF, nullptr, 0, grad + OFF_W0,
-                                                             grad + OFF_B0);
+  launch_wgrad<MW, MF>(c, A, n.X0, MF, nullptr, part, grad + OFF_W0, grad + OFF_B0);
   QP_CUDA(cudaGetLastError());
+  check_tc_flag(c);
   if (loss) {
     double h = 0.0;
     QP_CUDA(cudaMemcpyAsync(&h, lsum, sizeof(double), cudaMemcpyDeviceToHost, st));

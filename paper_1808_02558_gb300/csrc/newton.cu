@@ -696,6 +696,30 @@ __global__ void k_schur_blocks(PdipView v, double* __restrict__ H, float* __rest
   }
 }
 
+// Contact pass of the standalone FP64 apply with the Schur block of each
+// contact formed in registers from (gamma_c, lambda_c) (none when gamma is
+// null): y_c = U_c^T (w terms) + H_c x_c; dummy rows copy x.
+__global__ void k_contact_apply_h(SysView<double> s, const double* __restrict__ x, double* __restrict__ y,
+                                  const double* __restrict__ gamma, const double* __restrict__ lambda, double mu) {
+  const int n = s.Nc;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const long long row = (long long)s.slots * c;
+    contact_apply(s, plain(x), y, c);
+    if (gamma) {
+      double h[6];
+      schur_block(mu, gamma[row], gamma[row + 1], gamma[row + 2], lambda[c], lambda[n + c], h);
+      const double x0 = x[row], x1 = x[row + 1], x2 = x[row + 2];
+      y[row] += h[0] * x0 + h[1] * x1 + h[2] * x2;
+      y[row + 1] += h[1] * x0 + h[3] * x1 + h[4] * x2;
+      y[row + 2] += h[2] * x0 + h[4] * x1 + h[5] * x2;
+    }
+  }
+  const long long tail0 = (long long)s.slots * n;
+  for (long long i = tail0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.P;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
 // Diagonal entry (c, u) of N = D^T M^-1 D: sum over the contact's dynamic
 // bodies of 1/m + (rho x U_u)^T I^-1 (rho x U_u).
 __device__ __forceinline__ double diag_entry(const SysView<double>& s, int c, int u) {
@@ -1906,6 +1930,122 @@ __device__ void fused_apply(const SysView<T>& s, const Part& pt, const X& op, T*
   __syncthreads();
 }
 
+// y = S x (or N x without a state) in a single launch, the standalone form of
+// the fused operator (Eq. Ndef plus the Schur blocks of Sec. 3.3).  Block g
+// owns contacts [g chunk, (g+1) chunk) of the Morton order and the bodies they
+// touch (the partition of the pipelined solver): phase 1 forms w_b = M^-1 D_b x
+// for those bodies in shared memory (all incidences of each body, L lanes per
+// body, combined by shuffles; a border body is formed by every block that needs
+// it); phase 2 applies each contact's rows, with its 3x3 block H_c formed in
+// registers from (gamma_c, lambda_c) and never stored.  In FP32 the cone
+// function f_c (a difference of squares near the cone) is taken in FP64, the
+// rest of the block in FP32.  Dummy rows copy x.
+template <class T>
+__device__ __forceinline__ void schur_block_t(double mu, double gn, double g1, double g2, double lc, double ln,
+                                              T (&h)[6]) {
+  if constexpr (sizeof(T) == 8) {
+    schur_block(mu, gn, g1, g2, lc, ln, h);
+  } else {
+    const double fc = 0.5 * (g1 * g1 + g2 * g2 - mu * mu * gn * gn);
+    const float m2 = (float)(mu * mu);
+    const float q0 = -m2 * (float)gn, q1 = (float)g1, q2 = (float)g2;
+    const float l = (float)lc;
+    const float sc = l / (float)(-fc);
+    h[0] = -m2 * l + sc * q0 * q0 + (float)ln / (float)gn;
+    h[1] = sc * q0 * q1;
+    h[2] = sc * q0 * q2;
+    h[3] = l + sc * q1 * q1;
+    h[4] = sc * q1 * q2;
+    h[5] = l + sc * q2 * q2;
+  }
+}
+
+template <class T, bool WITH_H, int L>
+__global__ void __launch_bounds__(256) k_apply_one(SysView<T> s, Part pt, const T* __restrict__ x,
+                                                   T* __restrict__ y, const double* __restrict__ gamma,
+                                                   const double* __restrict__ lambda, double mu) {
+  static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "lanes: a power of two up to 32");
+  extern __shared__ __align__(16) unsigned char apply_smem[];
+  T* wl = reinterpret_cast<T*>(apply_smem);
+  const int g = blockIdx.x;
+  const int nbk = pt.nb[g];
+  const int per = blockDim.x / L;
+  const int lane = threadIdx.x & (L - 1);
+  const int* bl = pt.bodies + (long long)g * pt.maxb;
+  // phase 1: the loop bound is uniform over the block, so every lane reaches the shuffles
+  for (int b0 = 0; b0 < nbk; b0 += per) {
+    const int lb = b0 + (int)threadIdx.x / L;
+    T F0 = 0, F1 = 0, F2 = 0, Q0 = 0, Q1 = 0, Q2 = 0;
+    int b = 0;
+    if (lb < nbk) {
+      b = bl[lb];
+      const int e = __ldg(s.bptr + b + 1);
+      for (int k = __ldg(s.bptr + b) + lane; k < e; k += 2 * L) {
+        const int code[2] = {__ldg(s.inc + k), k + L < e ? __ldg(s.inc + k + L) : -1};
+        gather_batch<2>(s, plain(x), code, F0, F1, F2, Q0, Q1, Q2);
+      }
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+      F0 += __shfl_xor_sync(0xffffffffu, F0, o);
+      F1 += __shfl_xor_sync(0xffffffffu, F1, o);
+      F2 += __shfl_xor_sync(0xffffffffu, F2, o);
+      Q0 += __shfl_xor_sync(0xffffffffu, Q0, o);
+      Q1 += __shfl_xor_sync(0xffffffffu, Q1, o);
+      Q2 += __shfl_xor_sync(0xffffffffu, Q2, o);
+    }
+    if (lb < nbk && lane == 0) {
+      const T im = __ldg(s.inv_m + b), iI = __ldg(s.inv_I + b);
+      T* o = wl + (long long)lb * 8;
+      o[0] = im * F0;
+      o[1] = im * F1;
+      o[2] = im * F2;
+      o[3] = iI * Q0;
+      o[4] = iI * Q1;
+      o[5] = iI * Q2;
+    }
+  }
+  __syncthreads();
+  // phase 2: the block's contacts
+  const int n = s.Nc;
+  const int c0 = g * pt.chunk, c1 = min(n, c0 + pt.chunk);
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
+    T R[16];
+    load_rec(s.rec, c, R);
+    const int la = pt.cl[2 * c], lb = pt.cl[2 * c + 1];
+    const T* wb = wl + (long long)lb * 8;
+    T d0 = wb[0] + (wb[4] * R[14] - wb[5] * R[13]);
+    T d1 = wb[1] + (wb[5] * R[12] - wb[3] * R[14]);
+    T d2 = wb[2] + (wb[3] * R[13] - wb[4] * R[12]);
+    if (la >= 0) {
+      const T* wa = wl + (long long)la * 8;
+      d0 -= wa[0] + (wa[4] * R[11] - wa[5] * R[10]);
+      d1 -= wa[1] + (wa[5] * R[9] - wa[3] * R[11]);
+      d2 -= wa[2] + (wa[3] * R[10] - wa[4] * R[9]);
+    }
+    const long long row = (long long)s.slots * c;
+    const T x0 = x[row], x1 = x[row + 1], x2 = x[row + 2];
+    T y0 = R[0] * d0 + R[1] * d1 + R[2] * d2;
+    T y1 = R[3] * d0 + R[4] * d1 + R[5] * d2;
+    T y2 = R[6] * d0 + R[7] * d1 + R[8] * d2;
+    if constexpr (WITH_H) {
+      T h[6];
+      schur_block_t<T>(mu, gamma[row], gamma[row + 1], gamma[row + 2], lambda[c], lambda[n + c], h);
+      y0 += h[0] * x0 + h[1] * x1 + h[2] * x2;
+      y1 += h[1] * x0 + h[3] * x1 + h[4] * x2;
+      y2 += h[2] * x0 + h[4] * x1 + h[5] * x2;
+    }
+    y[row] = y0;
+    y[row + 1] = y1;
+    y[row + 2] = y2;
+    if (s.slots == 4) y[row + 3] = x[row + 3];
+  }
+  const long long tail0 = (long long)s.slots * n;
+  for (long long i = tail0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.P;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
 struct FusedArgs {
   SysView<double> s64;
   SysView<float> s32;
@@ -2515,17 +2655,18 @@ static void pdip_pre(qp_ctx* c, qp_state* st, int mode, const qp_pdip_opts* o) {
 }
 
 // Build (or reuse) the contact partition for a grid of G blocks.
-static void ensure_partition(qp_ctx* c, int G) {
-  if (c->part_G == G) return;
+// Contact partition into G chunks (one per block) with each block's body set.
+static void build_partition(qp_ctx* c, int G, qp::Buf& b_nb, qp::Buf& b_bodies, qp::Buf& b_cl, int& chunk_out,
+                            int& maxb_out, int& nbmax_out) {
   const int Nc = c->Nc;
   const int chunk = std::max(1, (Nc + G - 1) / G);
-  QP_REQUIRE(chunk <= 16384, QP_INVALID_ARG, "too many contacts per block for the fused Krylov kernel");
+  QP_REQUIRE(chunk <= 16384, QP_INVALID_ARG, "too many contacts per block for the fused operator");
   int n2 = 1;
   while (n2 < 2 * chunk) n2 <<= 1;
   const int maxb = 2 * chunk;
-  int* nb = static_cast<int*>(c->part_nb.ensure((size_t)G * sizeof(int)));
-  int* bodies = static_cast<int*>(c->part_bodies.ensure((size_t)G * maxb * sizeof(int)));
-  int* cl = static_cast<int*>(c->part_cl.ensure(2 * (size_t)std::max(Nc, 1) * sizeof(int)));
+  int* nb = static_cast<int*>(b_nb.ensure((size_t)G * sizeof(int)));
+  int* bodies = static_cast<int*>(b_bodies.ensure((size_t)G * maxb * sizeof(int)));
+  int* cl = static_cast<int*>(b_cl.ensure(2 * (size_t)std::max(Nc, 1) * sizeof(int)));
   const size_t smem = (size_t)n2 * sizeof(int);
   QP_CUDA(cudaFuncSetAttribute(k_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_partition<<<G, 1024, smem, c->stream>>>(Nc, c->M, chunk, maxb, c->ca.as<int>(), c->cb.as<int>(), nb, bodies, cl);
@@ -2535,10 +2676,50 @@ static void ensure_partition(qp_ctx* c, int G) {
   QP_CUDA(cudaStreamSynchronize(c->stream));
   int mx = 1;
   for (int v : h) mx = std::max(mx, v);
+  chunk_out = chunk;
+  maxb_out = maxb;
+  nbmax_out = mx;
+}
+
+static void ensure_partition(qp_ctx* c, int G) {
+  if (c->part_G == G) return;
+  build_partition(c, G, c->part_nb, c->part_bodies, c->part_cl, c->part_chunk, c->part_maxb, c->part_nbmax);
   c->part_G = G;
-  c->part_chunk = chunk;
-  c->part_maxb = maxb;
-  c->part_nbmax = mx;
+}
+
+// Partition of the standalone fused apply: chunks of about 256 contacts, the
+// block count a multiple of the SM count; cached per contact set.
+static Part apply_partition(qp_ctx* c) {
+  const int want = std::max(1, (c->Nc + 255) / 256);
+  const int G = ((want + c->num_sms - 1) / c->num_sms) * c->num_sms;
+  if (c->apart_G != G) {
+    build_partition(c, G, c->apart_nb, c->apart_bodies, c->apart_cl, c->apart_chunk, c->apart_maxb,
+                    c->apart_nbmax);
+    c->apart_G = G;
+  }
+  return Part{c->apart_chunk, c->apart_maxb, c->apart_nb.as<int>(), c->apart_bodies.as<int>(), c->apart_cl.as<int>()};
+}
+
+template <class T>
+static void launch_apply_one(qp_ctx* c, const SysView<T>& s, const T* x, T* y, const qp_state* st) {
+  if (c->Nc == 0) {
+    // no contacts: every row is a dummy row
+    QP_CUDA(cudaMemcpyAsync(y, x, (size_t)c->P * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    return;
+  }
+  const Part pt = apply_partition(c);
+  const size_t smem = (size_t)c->apart_nbmax * 8 * sizeof(T);
+  const int G = c->apart_G;
+  if (st) {
+    auto k = k_apply_one<T, true, 4>;
+    QP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<G, 256, smem, c->stream>>>(s, pt, x, y, st->gamma, st->lambda, c->mu);
+  } else {
+    auto k = k_apply_one<T, false, 4>;
+    QP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<G, 256, smem, c->stream>>>(s, pt, x, y, nullptr, nullptr, c->mu);
+  }
+  QP_CUDA(cudaGetLastError());
 }
 
 template <class T>
@@ -2985,9 +3166,22 @@ int newton_apply(qp_ctx_t c, const qp_state* st, const void* x, void* y, qp_dtyp
   check_ready(c, st);
   QP_REQUIRE(x && y && x != y, QP_INVALID_ARG, "newton_apply: null or aliased vectors");
   QP_REQUIRE(dt == QP_F64 || dt == QP_F32, QP_INVALID_ARG, "newton_apply: dtype must be QP_F64 or QP_F32");
-  if (st) launch_schur_blocks(c, st->gamma, st->lambda);
-  if (dt == QP_F64) launch_apply64(c, static_cast<const double*>(x), static_cast<double*>(y), st != nullptr);
-  else launch_apply32(c, static_cast<const float*>(x), static_cast<float*>(y), st != nullptr);
+  if (st) QP_REQUIRE(st->gamma && st->lambda, QP_INVALID_ARG, "newton_apply: state with null gamma/lambda");
+  if (dt == QP_F64) {
+    // FP64: two launches (the body gather once per body, then the contacts with
+    // their Schur blocks formed in registers); the one-launch form gathers the
+    // border bodies of every block again, which costs more on the narrow FP64 pipe
+    const SysView<double> s64 = view64(c, false);
+    if (c->M > 0)
+      k_body_gather_lanes<double, QP_APPLY_LANES><<<ceil_div((long long)c->M * QP_APPLY_LANES, 256), 256, 0,
+                                                   c->stream>>>(s64, static_cast<const double*>(x));
+    k_contact_apply_h<<<c->num_sms * 8, 256, 0, c->stream>>>(s64, static_cast<const double*>(x), static_cast<double*>(y),
+                                                             st ? st->gamma : nullptr, st ? st->lambda : nullptr, c->mu);
+    QP_CUDA(cudaGetLastError());
+  } else {
+    // FP32: one launch, the body intermediates in shared memory, the Schur blocks in registers
+    launch_apply_one<float>(c, view32(c, false), static_cast<const float*>(x), static_cast<float*>(y), st);
+  }
   API_END(c)
 }
 

@@ -62,6 +62,30 @@ def test_backward_matches_oracle(ctx):
         k += n
 
 
+def test_forward_and_backward_full_size(ctx):
+    """The 40^3 pile (191 806 contacts, 1499 row tiles of the tensor-core GEMM,
+    the last one partial): forward pass and gradient against the oracle, with
+    the same tolerances as the small case."""
+    pb = Problem(ctx, scene_for("pile40p", 1))
+    params = learned.init_params(9)
+    theta = bf16_round(to_np(params))
+    x = mpnn.features(pb.scene, pb.oc, pb.r, np.array(SCALE))
+    out = torch.empty(3 * pb.Nc, dtype=torch.float32, device="cuda")
+    pb.ctx.mpnn_forward(params, SCALE, out)
+    want, _ = mpnn.forward(theta, x, pb.oc.a, pb.oc.b, pb.scene.M)
+    assert_close(to_np(out), want.reshape(-1), 1e-4, floor_rel=1e-2, what="forward, 40^3 pile")
+    y = np.random.default_rng(2).standard_normal((pb.Nc, 3))
+    g = torch.empty_like(params)
+    loss = pb.ctx.mpnn_grad(params, SCALE, torch.tensor(y.reshape(-1), dtype=torch.float32, device="cuda"), g)
+    L, gw = mpnn.grad(theta, x, pb.oc.a, pb.oc.b, pb.scene.M, y.astype(np.float32).astype(np.float64))
+    assert abs(loss - L) <= 1e-5 * L
+    k = 0
+    for shp in mpnn.SHAPES:
+        n = int(np.prod(shp))
+        assert_close(to_np(g)[k:k + n], gw[k:k + n], 1e-3, floor_rel=1e-2, what=f"gradient block {shp}, 40^3 pile")
+        k += n
+
+
 def test_adam_step(ctx):
     pb, params, theta, x = setup(ctx)
     g = torch.randn_like(params)
