@@ -159,9 +159,10 @@ def job_throughput(local_units, local_ms, world):
 # ---------------------------------------------------------------------- our arm
 STATUS_NAMES = {0: "ok", -4: "not_converged", -5: "breakdown", -6: "linesearch_fail", -7: "timeout"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pcg<float, void>
-# launch of the 40^3 window, from an ncu capture of this kernel version (caches
-# flushed by ncu before the launch).  Reset to None when the kernel changes.
-KPCG_DRAM_BYTES_PER_LAUNCH = None  # recaptured after the reliable-update change
+# launch of the 40^3 window (mean of three consecutive launches), from an ncu capture of
+# this kernel version (caches flushed by ncu before each launch).  Reset to None when the
+# kernel changes.
+KPCG_DRAM_BYTES_PER_LAUNCH = 137.2e6
 
 
 # FP32 CUDA-core peak of the part from its unit counts: 152 SMs x 128 FP32 lanes x

@@ -1,0 +1,171 @@
+// Small dense FP64 linear algebra inside one thread block, shared by the QTT
+// compression, rounding and inversion: a block sum, and the symmetric
+// eigendecomposition by cyclic Jacobi with round-robin (parallel) rotation
+// order (Golub and Van Loan, Matrix Computations, Sec. 8.5), eigenvalues in
+// descending order, and the truncation rank of Sec. 3.1.
+//
+// GB300's FP64 pipe is narrow and an L2 round trip costs hundreds of cycles,
+// so a matrix of order n <= SYEV_SMEM_N is copied into shared memory (the
+// calling kernel launches with SYEV_SMEM_BYTES of dynamic shared memory) and
+// every rotation round works there; larger matrices are rotated in place in
+// global memory.
+#pragma once
+
+namespace qp {
+namespace dla {
+
+constexpr int SYEV_SMEM_N = 64;
+constexpr int SYEV_SMEM_BYTES = 2 * SYEV_SMEM_N * SYEV_SMEM_N * (int)sizeof(double);
+
+__device__ inline double block_sum(double v) {
+  __shared__ double sm[32];
+  __shared__ double res;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (threadIdx.x == 0) res = x;
+  }
+  __syncthreads();
+  double out = res;
+  __syncthreads();
+  return out;
+}
+
+// Round-robin pairing of m (even) players: round r, pair i.
+__device__ __forceinline__ void rr_pair(int m, int r, int i, int& p, int& q) {
+  if (i == 0) {
+    p = m - 1;
+    q = r;
+  } else {
+    p = (r + i) % (m - 1);
+    q = (r - i + (m - 1)) % (m - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Jacobi sweeps on A (n x n, row-major, destroyed); V accumulates the
+// rotations (starts as I).  A and V may live in shared or global memory.
+__device__ inline void jacobi_sweeps(double* A, double* V, int n) {
+  __shared__ double rc[256], rs[256];
+  __shared__ int rp[256], rq[256];
+  __shared__ int done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncthreads();
+  const int m = n + (n & 1);
+  const int npairs = m / 2;
+  for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
+    double off = 0.0, on = 0.0;
+    for (int i = tid; i < n * n; i += nt) {
+      const double a = A[i];
+      if (i / n == i % n) on += a * a;
+      else off += a * a;
+    }
+    off = block_sum(off);
+    on = block_sum(on);
+    if (tid == 0) done = (off <= 1e-30 * on) || (on == 0.0);
+    __syncthreads();
+    if (done) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int i = tid; i < npairs; i += nt) {
+        int p, q;
+        rr_pair(m, r, i, p, q);
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = A[p * n + q];
+          const double app = A[p * n + p], aqq = A[q * n + q];
+          if (apq != 0.0 && fabs(apq) > 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        rp[i] = p;
+        rq[i] = q;
+        rc[i] = c;
+        rs[i] = s;
+      }
+      __syncthreads();
+      // rows p, q  <-  J^T A
+      for (int idx = tid; idx < npairs * n; idx += nt) {
+        const int i = idx / n, j = idx - i * n;
+        const int p = rp[i], q = rq[i];
+        if (q >= n || rs[i] == 0.0) continue;
+        const double c = rc[i], s = rs[i];
+        const double a = A[p * n + j], b = A[q * n + j];
+        A[p * n + j] = c * a - s * b;
+        A[q * n + j] = s * a + c * b;
+      }
+      __syncthreads();
+      // columns p, q  <-  A J  and  V J
+      for (int idx = tid; idx < npairs * n; idx += nt) {
+        const int i = idx / n, j = idx - i * n;
+        const int p = rp[i], q = rq[i];
+        if (q >= n || rs[i] == 0.0) continue;
+        const double c = rc[i], s = rs[i];
+        double a = A[j * n + p], b = A[j * n + q];
+        A[j * n + p] = c * a - s * b;
+        A[j * n + q] = s * a + c * b;
+        a = V[j * n + p];
+        b = V[j * n + q];
+        V[j * n + p] = c * a - s * b;
+        V[j * n + q] = s * a + c * b;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Eigendecomposition of the symmetric n x n matrix A (row-major, destroyed):
+// w[0..n) the eigenvalues in descending order (ties by index), Vs the
+// eigenvectors as columns (row-major n x n); V is workspace n x n.  `smem`
+// points at SYEV_SMEM_BYTES of the block's dynamic shared memory, or is null.
+__device__ inline void syev(double* A, double* V, double* Vs, double* w, int n, double* smem) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* a = A;
+  double* v = V;
+  if (smem && n <= SYEV_SMEM_N) {
+    a = smem;
+    v = smem + n * n;
+    for (int i = tid; i < n * n; i += nt) a[i] = A[i];
+    __syncthreads();
+  }
+  jacobi_sweeps(a, v, n);
+  for (int i = tid; i < n; i += nt) {
+    const double di = a[i * n + i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = a[j * n + j];
+      if (dj > di || (dj == di && j < i)) ++rank;
+    }
+    w[rank] = di;
+    for (int row = 0; row < n; ++row) Vs[row * n + rank] = v[row * n + i];
+  }
+  __syncthreads();
+}
+
+// Smallest r with sqrt(sum_{l >= r} lambda_l) <= delta, 1 <= r <= min(rmax, n)
+// (eigenvalues of a Gram matrix, descending: the squared singular values).
+__device__ inline int trunc_rank(const double* lam, int n, double delta, int rmax) {
+  double tail = 0.0;
+  int r = n;
+  for (int k = n - 1; k >= 1; --k) {
+    tail += fmax(lam[k], 0.0);
+    if (sqrt(tail) <= delta) r = k;
+    else break;
+  }
+  if (r > rmax) r = rmax;
+  if (r < 1) r = 1;
+  return r;
+}
+
+}  // namespace dla
+}  // namespace qp

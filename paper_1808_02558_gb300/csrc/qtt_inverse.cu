@@ -18,123 +18,19 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "la_dev.cuh"
 
 namespace qp {
 namespace {
 
 constexpr int DT = 1024;
 
-__device__ double blk_sum(double v) {
-  __shared__ double sm[32];
-  __shared__ double res;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double x = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (threadIdx.x == 0) res = x;
-  }
-  __syncthreads();
-  double out = res;
-  __syncthreads();
-  return out;
-}
+__device__ inline double blk_sum(double v) { return dla::block_sum(v); }
 
-__device__ __forceinline__ void rr_pair2(int m, int r, int i, int& p, int& q) {
-  if (i == 0) {
-    p = m - 1;
-    q = r;
-  } else {
-    p = (r + i) % (m - 1);
-    q = (r - i + (m - 1)) % (m - 1);
-  }
-  if (p > q) {
-    int t = p;
-    p = q;
-    q = t;
-  }
-}
+extern __shared__ double la_smem[];
 
-// Symmetric eigendecomposition (cyclic Jacobi, round-robin order), FP64.
-__device__ void blk_syev(double* A, double* V, double* Vs, double* w, int n) {
-  __shared__ double rc[256], rs[256];
-  __shared__ int rp[256], rq[256];
-  __shared__ int done;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
-  __syncthreads();
-  const int m = n + (n & 1);
-  const int npairs = m / 2;
-  for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
-    double off = 0.0, on = 0.0;
-    for (int i = tid; i < n * n; i += nt) {
-      double a = A[i];
-      if (i / n == i % n) on += a * a;
-      else off += a * a;
-    }
-    off = blk_sum(off);
-    on = blk_sum(on);
-    if (tid == 0) done = (off <= 1e-30 * on) || (on == 0.0);
-    __syncthreads();
-    if (done) break;
-    for (int r = 0; r < m - 1; ++r) {
-      for (int i = tid; i < npairs; i += nt) {
-        int p, q;
-        rr_pair2(m, r, i, p, q);
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
-          if (fabs(apq) > 1e-300) {
-            double tau = (aqq - app) / (2.0 * apq);
-            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        rp[i] = p;
-        rq[i] = q;
-        rc[i] = c;
-        rs[i] = s;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < npairs * n; idx += nt) {
-        int i = idx / n, j = idx - i * n;
-        int p = rp[i], q = rq[i];
-        if (q >= n || rs[i] == 0.0) continue;
-        double c = rc[i], s = rs[i];
-        double a = A[p * n + j], b = A[q * n + j];
-        A[p * n + j] = c * a - s * b;
-        A[q * n + j] = s * a + c * b;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < npairs * n; idx += nt) {
-        int i = idx / n, j = idx - i * n;
-        int p = rp[i], q = rq[i];
-        if (q >= n || rs[i] == 0.0) continue;
-        double c = rc[i], s = rs[i];
-        double a = A[j * n + p], b = A[j * n + q];
-        A[j * n + p] = c * a - s * b;
-        A[j * n + q] = s * a + c * b;
-        a = V[j * n + p];
-        b = V[j * n + q];
-        V[j * n + p] = c * a - s * b;
-        V[j * n + q] = s * a + c * b;
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = tid; i < n; i += nt) {
-    double di = A[i * n + i];
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      double dj = A[j * n + j];
-      if (dj > di || (dj == di && j < i)) ++rank;
-    }
-    w[rank] = di;
-    for (int row = 0; row < n; ++row) Vs[row * n + rank] = V[row * n + i];
-  }
-  __syncthreads();
+__device__ inline void blk_syev(double* A, double* V, double* Vs, double* w, int n) {
+  dla::syev(A, V, Vs, w, n, la_smem);
 }
 
 struct DmrgArgs {
@@ -298,17 +194,8 @@ __device__ double local_solve(const DmrgArgs& a, int k, int rl, int rr, float* x
   return rn / bn;
 }
 
-__device__ int trunc_rank2(const double* lam, int n, double delta, int rmax) {
-  double tail = 0.0;
-  int r = n;
-  for (int k = n - 1; k >= 1; --k) {
-    tail += fmax(lam[k], 0.0);
-    if (sqrt(tail) <= delta) r = k;
-    else break;
-  }
-  if (r > rmax) r = rmax;
-  if (r < 1) r = 1;
-  return r;
+__device__ inline int trunc_rank2(const double* lam, int n, double delta, int rmax) {
+  return dla::trunc_rank(lam, n, delta, rmax);
 }
 
 // PhiL[k+1], PsiL[k+1] from PhiL[k], PsiL[k] and core X_k (rank rl x 4 x rn)
@@ -716,7 +603,8 @@ qp_qtt* inverse_impl(qp_ctx* c, qp_qtt* S, double eps, int rmax, int sweeps, qp_
   a.Vs = Gb + 2 * gcap;
   a.ev = Gb + 3 * gcap;
   a.norms = Gb + 3 * gcap + 4 * R;
-  k_dmrg<<<1, DT, 0, st>>>(a);
+  QP_CUDA(cudaFuncSetAttribute(k_dmrg, cudaFuncAttributeMaxDynamicSharedMemorySize, dla::SYEV_SMEM_BYTES));
+  k_dmrg<<<1, DT, dla::SYEV_SMEM_BYTES, st>>>(a);
   QP_CUDA(cudaGetLastError());
   std::vector<int> ro(d + 1);
   QP_CUDA(cudaMemcpyAsync(ro.data(), xr_dev, (d + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -1,7 +1,7 @@
 // TT rounding (Sec. 3.1 truncation rule, Oseledets 2011 rounding) and the QTT
 // compression of the Schur matrix (Sec. 3.2 tensorisation, Alg. 1 TT-SVD).
 //
-// Small dense linear algebra runs in FP64 inside one thread block: symmetric
+// Small dense linear algebra runs in FP64 inside one thread block (la_dev.cuh): symmetric
 // eigendecompositions by cyclic Jacobi with round-robin (parallel) rotation
 // order (Golub and Van Loan, Matrix Computations, Sec. 8.5), and the SVD of a
 // tall matrix C through the eigenpairs of its Gram matrix C^T C.
@@ -17,144 +17,22 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "la_dev.cuh"
 
 namespace qp {
 namespace {
 
 constexpr int LT = 1024;  // threads of the one-block kernels
 
-__device__ double cta_sum(double v) {
-  __shared__ double sm[32];
-  __shared__ double res;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double x = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (threadIdx.x == 0) res = x;
-  }
-  __syncthreads();
-  double out = res;
-  __syncthreads();
-  return out;
-}
+using dla::trunc_rank;
 
-// Round-robin pairing of m (even) players: round r, pair i.
-__device__ __forceinline__ void rr_pair(int m, int r, int i, int& p, int& q) {
-  if (i == 0) {
-    p = m - 1;
-    q = r;
-  } else {
-    p = (r + i) % (m - 1);
-    q = (r - i + (m - 1)) % (m - 1);
-  }
-  if (p > q) {
-    int t = p;
-    p = q;
-    q = t;
-  }
-}
+__device__ inline double cta_sum(double v) { return dla::block_sum(v); }
 
-// Eigen-decomposition of the symmetric n x n matrix A (row-major, destroyed).
-// On return w[0..n) holds the eigenvalues in descending order and Vs the
-// matching eigenvectors as columns (row-major n x n).  V is workspace n x n.
-__device__ void cta_syev(double* A, double* V, double* Vs, double* w, int n) {
-  __shared__ double rc[256], rs[256];
-  __shared__ int rp[256], rq[256];
-  __shared__ int done;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
-  __syncthreads();
-  const int m = n + (n & 1);
-  const int npairs = m / 2;
-  for (int sweep = 0; sweep < 40 && n > 1; ++sweep) {
-    double off = 0.0, on = 0.0;
-    for (int i = tid; i < n * n; i += nt) {
-      double a = A[i];
-      if (i / n == i % n) on += a * a;
-      else off += a * a;
-    }
-    off = cta_sum(off);
-    on = cta_sum(on);
-    if (tid == 0) done = (off <= 1e-30 * on) || (on == 0.0);
-    __syncthreads();
-    if (done) break;
-    for (int r = 0; r < m - 1; ++r) {
-      for (int i = tid; i < npairs; i += nt) {
-        int p, q;
-        rr_pair(m, r, i, p, q);
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = A[p * n + q];
-          double app = A[p * n + p], aqq = A[q * n + q];
-          if (apq != 0.0 && fabs(apq) > 1e-300) {
-            double tau = (aqq - app) / (2.0 * apq);
-            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        rp[i] = p;
-        rq[i] = q;
-        rc[i] = c;
-        rs[i] = s;
-      }
-      __syncthreads();
-      // rows p, q  <-  J^T A
-      for (int idx = tid; idx < npairs * n; idx += nt) {
-        int i = idx / n, j = idx - i * n;
-        int p = rp[i], q = rq[i];
-        if (q >= n || rs[i] == 0.0) continue;
-        double c = rc[i], s = rs[i];
-        double a = A[p * n + j], b = A[q * n + j];
-        A[p * n + j] = c * a - s * b;
-        A[q * n + j] = s * a + c * b;
-      }
-      __syncthreads();
-      // columns p, q  <-  A J  and  V J
-      for (int idx = tid; idx < npairs * n; idx += nt) {
-        int i = idx / n, j = idx - i * n;
-        int p = rp[i], q = rq[i];
-        if (q >= n || rs[i] == 0.0) continue;
-        double c = rc[i], s = rs[i];
-        double a = A[j * n + p], b = A[j * n + q];
-        A[j * n + p] = c * a - s * b;
-        A[j * n + q] = s * a + c * b;
-        a = V[j * n + p];
-        b = V[j * n + q];
-        V[j * n + p] = c * a - s * b;
-        V[j * n + q] = s * a + c * b;
-      }
-      __syncthreads();
-    }
-  }
-  // sort descending (rank of each eigenvalue; ties by index)
-  for (int i = tid; i < n; i += nt) {
-    double di = A[i * n + i];
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      double dj = A[j * n + j];
-      if (dj > di || (dj == di && j < i)) ++rank;
-    }
-    w[rank] = di;
-    for (int row = 0; row < n; ++row) Vs[row * n + rank] = V[row * n + i];
-  }
-  __syncthreads();
-}
+// dynamic shared memory of the one-block kernels (the eigensolver's staging area)
+extern __shared__ double la_smem[];
 
-// Smallest r with sqrt(sum_{l >= r} lambda_l) <= delta, 1 <= r <= min(rmax, n).
-__device__ int trunc_rank(const double* lam, int n, double delta, int rmax) {
-  double tail = 0.0;
-  int r = n;
-  for (int k = n - 1; k >= 1; --k) {
-    tail += fmax(lam[k], 0.0);
-    if (sqrt(tail) <= delta) r = k;
-    else break;
-  }
-  if (r > rmax) r = rmax;
-  if (r < 1) r = 1;
-  return r;
+__device__ inline void cta_syev(double* A, double* V, double* Vs, double* w, int n) {
+  dla::syev(A, V, Vs, w, n, la_smem);
 }
 
 // ---------------------------------------------------------------- rounding
@@ -455,6 +333,177 @@ __global__ void __launch_bounds__(LT) k_eig_trunc(EigArgs e) {
   if (threadIdx.x == 0) *e.rank_out = trunc_rank(e.w, e.n, e.delta, e.rmax);
 }
 
+// ---------------------------------------------------------------- multi-block Jacobi
+// Gram matrices of order n > SYEV_SMEM_N (ranks above 16) do not fit in one
+// block's shared memory, and one block rotating them in global memory spends
+// most of its time waiting on L2.  Their rotation rounds spread over a
+// cooperative grid: in round r every block forms the round's rotations from A
+// (the same values in every block), the rows of B = J^T A are written from A,
+// a grid barrier, then A = B J and V = V J, a grid barrier.  B is a second
+// buffer so that no block rotates rows of A that another block is still
+// reading for its rotations.  The sweeps, the convergence test and the sorted
+// output are those of the one-block solver; every wait is bounded (QP_TIMEOUT).
+struct EigCoopArgs {
+  double* A;
+  double* B;
+  double* V;
+  double* Vs;
+  double* w;
+  int n;
+  double delta;
+  int rmax;
+  int* rank_out;
+  DevCtl* ctl;
+  double* part;  // 2 per block
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Counter barrier over the cooperative grid (the counter starts at 0); thread
+// 0 of each block counts the generations in `gen`.  False on timeout or when
+// another block has recorded an error.
+__device__ bool coop_barrier(DevCtl* ctl, unsigned& gen) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gen += 1u;
+    red_release_add_u32(&ctl->bar_count, 1u);
+    const unsigned target = gen * gridDim.x;
+    const long long t0 = clock64();
+    ok = 1;
+    while ((int)(ld_acquire_u32(&ctl->bar_count) - target) < 0) {
+      if (*(volatile int*)&ctl->err) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > 4000000000LL) {
+        atomicCAS(&ctl->err, 0, QP_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_eig_coop(EigCoopArgs e) {
+  __shared__ double rc[256], rs[256];
+  __shared__ int rp[256], rq[256];
+  __shared__ int s_done;
+  unsigned gen = 0;
+  const int n = e.n;
+  const long long nn = (long long)n * n;
+  const long long gsz = (long long)gridDim.x * blockDim.x;
+  const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double* A = e.A;
+  double* B = e.B;
+  double* V = e.V;
+  for (long long i = gtid; i < nn; i += gsz) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  const int m = n + (n & 1), npairs = m / 2;
+  bool good = coop_barrier(e.ctl, gen);
+  for (int sweep = 0; good && sweep < 40 && n > 1; ++sweep) {
+    double off = 0.0, on = 0.0;
+    for (long long i = gtid; i < nn; i += gsz) {
+      const double a = A[i];
+      if (i / n == i % n) on += a * a;
+      else off += a * a;
+    }
+    off = dla::block_sum(off);
+    on = dla::block_sum(on);
+    if (threadIdx.x == 0) {
+      e.part[2 * blockIdx.x] = off;
+      e.part[2 * blockIdx.x + 1] = on;
+    }
+    if (!(good = coop_barrier(e.ctl, gen))) break;
+    if (threadIdx.x == 0) {
+      double so = 0.0, sn = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) {
+        so += *(volatile double*)&e.part[2 * b];
+        sn += *(volatile double*)&e.part[2 * b + 1];
+      }
+      s_done = (so <= 1e-30 * sn) || (sn == 0.0);
+    }
+    __syncthreads();
+    if (s_done) break;
+    for (int r = 0; r < m - 1 && good; ++r) {
+      for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+        int p, q;
+        dla::rr_pair(m, r, i, p, q);
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = A[p * n + q];
+          const double app = A[p * n + p], aqq = A[q * n + q];
+          if (apq != 0.0 && fabs(apq) > 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        rp[i] = p;
+        rq[i] = q;
+        rc[i] = c;
+        rs[i] = s;
+      }
+      __syncthreads();
+      // B = J^T A: rows p, q of each pair (an unpaired row is copied)
+      for (long long idx = gtid; idx < (long long)npairs * n; idx += gsz) {
+        const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+        const int p = rp[i], q = rq[i];
+        if (q >= n) {
+          B[p * n + j] = A[p * n + j];
+          continue;
+        }
+        const double c = rc[i], s = rs[i];
+        const double a = A[p * n + j], b = A[q * n + j];
+        B[p * n + j] = c * a - s * b;
+        B[q * n + j] = s * a + c * b;
+      }
+      if (!(good = coop_barrier(e.ctl, gen))) break;
+      // A = B J and V = V J: columns p, q of each pair
+      for (long long idx = gtid; idx < (long long)npairs * n; idx += gsz) {
+        const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+        const int p = rp[i], q = rq[i];
+        if (q >= n) {
+          A[j * n + p] = B[j * n + p];
+          continue;
+        }
+        const double c = rc[i], s = rs[i];
+        double a = B[j * n + p], b = B[j * n + q];
+        A[j * n + p] = c * a - s * b;
+        A[j * n + q] = s * a + c * b;
+        a = V[j * n + p];
+        b = V[j * n + q];
+        V[j * n + p] = c * a - s * b;
+        V[j * n + q] = s * a + c * b;
+      }
+      good = coop_barrier(e.ctl, gen);
+    }
+  }
+  if (!good) return;
+  // eigenvalues in descending order (ties by index), eigenvectors as columns
+  for (long long i = gtid; i < n; i += gsz) {
+    const double di = A[i * n + i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = A[(long long)j * n + j];
+      if (dj > di || (dj == di && j < i)) ++rank;
+    }
+    e.w[rank] = di;
+    for (int row = 0; row < n; ++row) e.Vs[(long long)row * n + rank] = V[(long long)row * n + i];
+  }
+  if (!coop_barrier(e.ctl, gen)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *e.rank_out = trunc_rank(e.w, n, e.delta, e.rmax);
+}
+
 // core_k(a, b, al) = Vs[(b*r + al), a]  for a < rnew
 __global__ void k_core_from_V(int n, int r, int rnew, const double* __restrict__ Vs, double* __restrict__ core) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rnew * n; i += gridDim.x * blockDim.x) {
@@ -544,7 +593,8 @@ qp_qtt* tt_round_impl(qp_ctx* c, const qp_qtt* A, double eps, int rmax) {
     QP_CUDA(cudaMemcpyAsync(cores + (size_t)k * cap, A->cores + A->offset[k],
                             (A->offset[k + 1] - A->offset[k]) * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   QP_CUDA(cudaMemcpyAsync(ranks, A->ranks.data(), (d + 1) * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  k_tt_round<<<1, LT, 0, c->stream>>>(a);
+  QP_CUDA(cudaFuncSetAttribute(k_tt_round, cudaFuncAttributeMaxDynamicSharedMemorySize, dla::SYEV_SMEM_BYTES));
+  k_tt_round<<<1, LT, dla::SYEV_SMEM_BYTES, c->stream>>>(a);
   QP_CUDA(cudaGetLastError());
   std::vector<int> r(d + 1);
   QP_CUDA(cudaMemcpyAsync(r.data(), ranks, (d + 1) * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -614,7 +664,8 @@ qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax, const double
   tmp = c->scratch[1].ensure(tb);
   QP_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tb, key, key_s, val, val_s, nent, 0, 2 * d, st));
   // 3. ||S||_F and delta
-  double* part = static_cast<double*>(w.tmp.ensure(1024 * sizeof(double)));
+  // [0, 256): norm partials; 512: rank; [1024, 1024 + 2 x blocks): eigensolver partials
+  double* part = static_cast<double*>(w.tmp.ensure((1024 + 4096) * sizeof(double)));
   k_sumsq<<<256, 256, 0, st>>>(nent, val_s, part);
   std::vector<double> hp(256);
   QP_CUDA(cudaMemcpyAsync(hp.data(), part, 256 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -669,8 +720,26 @@ qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax, const double
     ea.rmax = rmax;
     int* rk_dev = reinterpret_cast<int*>(static_cast<double*>(w.tmp.p) + 512);
     ea.rank_out = rk_dev;
-    k_eig_trunc<<<1, LT, 0, st>>>(ea);
-    QP_CUDA(cudaGetLastError());
+    if (n <= dla::SYEV_SMEM_N) {
+      QP_CUDA(cudaFuncSetAttribute(k_eig_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize, dla::SYEV_SMEM_BYTES));
+      k_eig_trunc<<<1, LT, dla::SYEV_SMEM_BYTES, st>>>(ea);
+      QP_CUDA(cudaGetLastError());
+    } else {
+      // larger Gram matrices: the rotation rounds on a cooperative grid
+      EigCoopArgs ec{G, static_cast<double*>(w.misc.ensure((size_t)n * n * sizeof(double))), ea.V, ea.Vs, ea.w, n,
+                     delta, rmax, rk_dev, c->ctl.as<DevCtl>(),
+                     static_cast<double*>(w.tmp.p) + 1024};
+      QP_CUDA(cudaMemsetAsync(c->ctl.p, 0, sizeof(DevCtl), st));
+      int per_sm = 0;
+      QP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eig_coop, 256, 0));
+      const int grid = std::min(c->num_sms * std::max(per_sm, 1), std::max(1, (n / 2) * n / 256));
+      void* args[] = {&ec};
+      QP_CUDA(cudaLaunchCooperativeKernel((const void*)k_eig_coop, dim3(grid), dim3(256), args, 0, st));
+      DevCtl hc;
+      QP_CUDA(cudaMemcpyAsync(&hc, c->ctl.p, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+      QP_CUDA(cudaStreamSynchronize(st));
+      QP_REQUIRE(hc.err == 0, QP_TIMEOUT, "qtt_compress: eigensolver grid barrier wait expired");
+    }
     int rnew = 1;
     QP_CUDA(cudaMemcpyAsync(&rnew, rk_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     QP_CUDA(cudaStreamSynchronize(st));
