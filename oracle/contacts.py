@@ -11,10 +11,14 @@ readings taken where the paper is silent are:
 
   * normal n = (x_b - x_a)/d; the floor is body "a" (static, index M), n = +z;
   * contact point p = x_a + n (r_a + Phi/2); for the floor p = (x, y, z_f + Phi/2);
+  * side walls (an extension for boxed scenes): axis-aligned static planes
+    x_axis = offset with the box on the side `sign`, Phi = sign (x_axis - offset) - r,
+    n = sign e_axis, p on that axis = offset + sign Phi/2; static body M as well;
   * tangents: e = coordinate axis minimising |n_e| (lowest index on ties),
     t1 = (n x e)/|n x e|, t2 = n x t1;
   * order: Morton key of p quantised to 21 bits per axis over the bounding box of
-    all contact points (x -> bit 3k, y -> 3k+1, z -> 3k+2), ties broken by (a, b).
+    all contact points (x -> bit 3k, y -> 3k+1, z -> 3k+2), ties broken by (a, b),
+    a static plane counting as M (floor) or M + 1 + w (wall w).
 
 Every floating-point expression is written with an explicit evaluation order
 (numpy never contracts a*b+c into an FMA), so the integer results (pair list and
@@ -169,15 +173,35 @@ def detect(scene, pairs: np.ndarray | None = None) -> Contacts:
     n_f[:, 2] = 1.0
     p_f = np.stack([pos[fb, 0], pos[fb, 1], fz + phi_f * 0.5], axis=1)
 
-    a = np.concatenate([pa, np.full(fb.size, M, dtype=np.int64)])
-    b = np.concatenate([pb, fb])
-    phi = np.concatenate([phi_p, phi_f])
-    n = np.concatenate([n_p, n_f]).reshape(-1, 3)
-    p = np.concatenate([p_p, p_f]).reshape(-1, 3)
+    # sphere-wall contacts: static planes x_axis = offset, the box on the side of
+    # `sign`; like the floor, a wall is body "a" (static, index M), its normal
+    # sign * e_axis points into the box, and p = offset + sign * Phi/2 on that axis
+    aw, bw, phw, nw, pw = [], [], [], [], []
+    for w, (axis, sign, off) in enumerate(getattr(scene, "walls", ()) or ()):
+        x = pos[:, axis]
+        ph_all = ((x - off) if sign > 0 else (off - x)) - rad
+        sel = np.nonzero(ph_all <= delta)[0].astype(np.int64)
+        ph = ph_all[sel]
+        nv = np.zeros((sel.size, 3))
+        nv[:, axis] = float(sign)
+        pv = pos[sel].copy()
+        pv[:, axis] = off + ((ph * 0.5) if sign > 0 else -(ph * 0.5))
+        aw.append(np.full(sel.size, M + 1 + w, dtype=np.int64))  # plane index breaks ties below
+        bw.append(sel)
+        phw.append(ph)
+        nw.append(nv)
+        pw.append(pv)
+
+    a = np.concatenate([pa, np.full(fb.size, M, dtype=np.int64)] + aw)
+    b = np.concatenate([pb, fb] + bw)
+    phi = np.concatenate([phi_p, phi_f] + phw)
+    n = np.concatenate([n_p, n_f] + nw).reshape(-1, 3)
+    p = np.concatenate([p_p, p_f] + pw).reshape(-1, 3)
 
     key = morton_keys(p)
     order = np.lexsort((b, a, key))
     a, b, phi, n, p, key = a[order], b[order], phi[order], n[order], p[order], key[order]
+    a = np.minimum(a, M)  # every static plane is body M
     t1, t2 = tangent_frame(n)
     stat = a == M
     xa = np.where(stat[:, None], 0.0, pos[np.minimum(a, M - 1)] if M > 0 else 0.0)

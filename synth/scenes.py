@@ -76,6 +76,7 @@ class Scene:
     mu: float = 0.5
     delta: float = 0.0
     seed: int = 0
+    walls: tuple = ()  # side walls (axis, sign, offset): plane x_axis = offset, box on the side of sign
     mass: np.ndarray = field(init=False)
     inv_mass: np.ndarray = field(init=False)
     inv_inertia: np.ndarray = field(init=False)
@@ -138,13 +139,37 @@ def column_scene(nx: int, height: int, seed: int, *, lateral: float = 1.03, spac
                  radius=np.full(M, 0.5), mu=mu, dt=dt, delta=0.0, seed=seed)
 
 
+def box_scene(seed: int, *, n: int = 40, layers: int = 40, spacing: float = 1.0, lift: float = 2.0,
+              jitter: float = 0.01, vel_sigma: float = 0.1, mu: float = 0.5, dt: float = 1e-3,
+              delta: float = 0.21, name: str | None = None) -> Scene:
+    """Polydisperse spheres (radius U[0.4, 0.6], density 1) in a walled box of
+    n x n x 2n: an n x n x layers jittered lattice, `spacing` apart across and
+    `lift` apart in height (the layers fall onto each other under gravity),
+    velocities N(0, vel_sigma^2), side walls at x, y = -spacing/2 and
+    (n - 1/2) spacing, the floor at z = 0 under the lowest layer's centres at 0.5.
+    Body id = i + n*j + n*n*k."""
+    M = n * n * layers
+    k, j, i = np.meshgrid(np.arange(layers), np.arange(n), np.arange(n), indexing="ij")
+    site = np.stack([i.ravel() * spacing, j.ravel() * spacing, k.ravel() * lift], axis=1).astype(np.float64)
+    jit = (2.0 * splitmix64_uniform(seed, 1, 3 * M) - 1.0).reshape(M, 3) * jitter
+    pos = site + np.array([0.0, 0.0, 0.5]) + jit
+    vel = normal_vector(seed, 2, 3 * M, vel_sigma).reshape(M, 3)
+    radius = 0.4 + 0.2 * splitmix64_uniform(seed, 3, M)
+    lo, hi = -0.5 * spacing, (n - 0.5) * spacing
+    walls = ((0, 1, lo), (0, -1, hi), (1, 1, lo), (1, -1, hi))
+    return Scene(name=name or f"box{n}-s{seed}", pos=pos, vel=vel, omega=np.zeros((M, 3)), radius=radius, mu=mu,
+                 dt=dt, delta=delta, seed=seed, walls=walls)
+
+
 # Named workloads: the small FP64 pile, the 20^3 pile, the 40^3 polydisperse pile,
-# and 16 x 16 columns of 10 spheres (every contact loaded; 2560 contacts, 2^13).
+# 16 x 16 columns of 10 spheres (every contact loaded; 2560 contacts, 2^13), and
+# 64 000 polydisperse spheres falling in a walled 40 x 40 x 80 box.
 SCENES = {
     "pile8": dict(n=8, polydisperse=False),
     "pile20": dict(n=20, polydisperse=False),
     "pile40p": dict(n=40, polydisperse=True),
     "stack16": dict(columns=16, height=10),
+    "box40": dict(box=40),
 }
 
 
@@ -152,6 +177,8 @@ def scene_for(name: str, seed: int = 1) -> Scene:
     spec = SCENES[name]
     if "columns" in spec:
         return column_scene(spec["columns"], spec["height"], seed, name=f"{name}-s{seed}")
+    if "box" in spec:
+        return box_scene(seed, n=spec["box"], name=f"{name}-s{seed}")
     return lattice_scene(spec["n"], seed, spec["polydisperse"], name=f"{name}-s{seed}")
 
 

@@ -88,3 +88,51 @@ def test_order_is_key_then_bodies():
     trip = list(zip(c.key.tolist(), c.a.tolist(), c.b.tolist()))
     assert trip == sorted(trip)
     assert len(set(zip(c.a.tolist(), c.b.tolist()))) == c.Nc
+
+
+def test_wall_contacts_hand_computed():
+    """One sphere against each side wall (an extension of the floor rule): gap
+    sign (x_axis - offset) - r, normal sign e_axis into the box, contact point
+    offset + sign Phi/2 on that axis, arm of the static wall zero."""
+    from synth import Scene
+
+    walls = ((0, 1, -1.0), (0, -1, 4.0), (1, 1, 0.0), (1, -1, 2.5))
+    pos = np.array([[-0.55, 1.0, 3.0], [3.6, 1.0, 3.0], [1.5, 0.38, 3.0], [1.5, 2.05, 3.0]])
+    rad = np.array([0.5, 0.45, 0.4, 0.5])
+    s = Scene(name="walls", pos=pos, vel=np.zeros((4, 3)), omega=np.zeros((4, 3)), radius=rad, delta=0.05,
+              walls=walls)
+    c = oc.detect(s)
+    assert c.Nc == 4 and np.all(c.a == 4)
+    # the midpoint between the sphere surface and the wall
+    want = {0: (-0.05, [1, 0, 0], [-1.025, 1.0, 3.0]), 1: (-0.05, [-1, 0, 0], [4.025, 1.0, 3.0]),
+            2: (-0.02, [0, 1, 0], [1.5, -0.01, 3.0]), 3: (-0.05, [0, -1, 0], [1.5, 2.525, 3.0])}
+    for k in range(4):
+        b = int(c.b[k])
+        phi, n, p = want[b]
+        assert abs(c.phi[k] - phi) < 1e-12
+        assert np.allclose(c.n[k], n) and np.allclose(c.p[k], p, atol=1e-12)
+        assert np.all(c.ra[k] == 0.0)
+        assert np.allclose(c.rb[k], np.array(p) - pos[b], atol=1e-12)
+        assert abs(np.dot(c.t1[k], c.n[k])) < 1e-15 and abs(np.dot(c.t2[k], c.n[k])) < 1e-15
+    # a sphere out of reach of every wall has no contact
+    s2 = Scene(name="free", pos=np.array([[1.5, 1.2, 3.0]]), vel=np.zeros((1, 3)), omega=np.zeros((1, 3)),
+               radius=np.array([0.5]), delta=0.05, walls=walls)
+    assert oc.detect(s2).Nc == 0
+
+
+def test_box_scene_counts_and_order():
+    """Box scene: the floor under every bottom sphere and one wall contact per
+    outer sphere and side; the order is total ((key, a, b) with the plane index
+    breaking ties) and every pair is found by the brute-force search."""
+    from synth import box_scene
+
+    s = box_scene(1, n=6, layers=4)
+    c = oc.detect(s)
+    stat = c.a == s.M
+    n, layers = 6, 4
+    assert int(stat.sum()) == n * n + 4 * n * layers
+    floor = stat & (c.n[:, 2] == 1.0)
+    assert int(floor.sum()) == n * n
+    pairs = oc.candidate_pairs_bruteforce(s.pos, s.radius, s.delta)
+    assert int((~stat).sum()) == len(pairs)
+    assert np.all(np.diff(c.key.astype(np.float64)) >= 0)
