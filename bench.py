@@ -412,6 +412,7 @@ def run_ours(args):
     learned_out = learned_leg(args, binding, workload) if args.learned_steps > 0 else None
     if learned_out is not None:
         learned_out["network_at_bench_scale"] = mpnn_scale_leg(binding, workload, scene, flush, stream)
+    box_out = box_leg(args, binding, workload, flush, stream) if args.box_steps > 0 else None
     configs_out = None
     if args.config_legs:
         cpu_ok = rank == 0 and not args.no_cpu_baseline
@@ -452,6 +453,7 @@ def run_ours(args):
         "batched": batch_out,
         "learned_warm_start": learned_out,
         "configs": configs_out,
+        "box_time_stepping": box_out,
     }
     if rank == 0 and not args.no_cpu_baseline:
         its = gpu_window_iterates(ctx, st, gamma, lam, opts, args.window, ok, Nc)
@@ -945,6 +947,191 @@ def time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream):
             "note": "Jacobi-PCG windows; warm start = previous impulses of persisting pairs moved into the cone"}
 
 
+def box_leg(args, binding, workload, flush, stream):
+    """Time stepping of 64 000 polydisperse spheres falling in the walled 40 x 40
+    x 80 box (Sec. 2.3), args.box_steps steps of seed 1.  A step: assemble (pairs,
+    floor, side walls), start the PDIP from the previous step's impulses on the
+    persisting pairs (cold at the first step), args.box_window PDIP iterations
+    with mixed-precision Jacobi-PCG Newton solves at 1e-8, advance.  Alongside,
+    outside the step time:
+    * QTT reuse across steps (Sec. 3.3): the inverse of every step's first Newton
+      system is refreshed (compressed, then inverted warm-started from the
+      previous step's inverse) and used by one QTT-PCG solve; every 25th step
+      the same refresh and solve run from scratch in a fresh context;
+    * learned start: the network is trained on the window solutions of the
+      first args.box_train_steps steps of seeds 2 and 3 and, every 10th step of
+      seed 1, starts the same window, compared with the cold start and with the
+      warm start of the trajectory (gap and dual residual after the window)."""
+    import torch
+
+    from paper_1808_02558_gb300 import learned
+    from synth import scene_for
+
+    ok = (binding.QP_NOT_CONVERGED, binding.QP_LINESEARCH_FAIL)
+    W = args.box_window
+    scale = [1.0, 1.0, 1.0, 0.05, 0.05, 0.05, 0.05, 2.0]
+
+    def opts_for(c):
+        return c.pdip_opts(c.solve_opts(tol=1e-8, maxit=200000, mixed=1, inner_tol=1e-3, max_outer=60))
+
+    def qtt_opts(c):
+        so = c.solve_opts(binding.QP_QTT_PCG, None, tol=1e-8, maxit=args.qtt_maxit, mixed=1, inner_tol=1e-3,
+                          max_outer=60, core_dtype=binding.QP_BF16)
+        return c.pdip_opts(so, qtt_refresh=1, qtt_eps=args.qtt_eps, qtt_rmax=args.qtt_rmax)
+
+    def fresh_state(con):
+        g = torch.zeros(con.P, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(2 * con.Nc, dtype=torch.float64, device="cuda")
+        return g, lam, binding.Context.state(g, lam)
+
+    def trajectory(seed, steps, hook=None, timed=False):
+        sc = scene_for("box40", seed)
+        ctx = binding.Context()
+        dev_s = workload.scene_to_device(sc, "cuda")
+        opts = opts_for(ctx)
+        prev, rows = None, []
+        for step in range(steps):
+            dev_before = {k: v.clone() for k, v in dev_s.items()} if hook else None
+            if timed:
+                flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            con = ctx.assemble(dev_s, sc.floor_z, sc.gravity, sc.dt, sc.delta, sc.mu, 3, sc.walls)
+            ev[1].record(stream)
+            g, lam, st = fresh_state(con)
+            if prev is None:
+                ctx.pdip_init(st, 1.0)
+            else:
+                ctx.pdip_init_warm(st, prev[0], prev[1], prev[2], 3)
+            stats = [ctx.pdip_step(st, opts, allow=ok) for _ in range(W)]
+            ev[2].record(stream)
+            ab = (workload.view(con, "body_a"), workload.view(con, "body_b"))
+            eta, rd = ctx.pdip_measure(st)
+            side = hook(step, ctx, con, g, dev_before, sc) if hook else None
+            ev[3].record(stream)
+            ctx.advance(st)
+            ev4 = torch.cuda.Event(enable_timing=True)
+            ev4.record(stream)
+            ev4.synchronize()
+            keys = set(zip(ab[0].tolist(), ab[1].tolist()))
+            rows.append({"step": step, "contacts": con.Nc, "padded_unknowns": con.P,
+                         "persisting": None if prev is None else len(keys & prev[3]) / max(1, len(keys)),
+                         "ms_assemble": ev[0].elapsed_time(ev[1]), "ms_pdip_window": ev[1].elapsed_time(ev[2]),
+                         "ms_advance": ev[3].elapsed_time(ev4), "eta": eta, "r_dual": rd,
+                         "pdip_ok": sum(int(s_.status == binding.QP_OK) for s_ in stats),
+                         "solves_converged": sum(int(s_.solve.status == binding.QP_OK and s_.solve.rel_res <= 1e-8)
+                                                 for s_ in stats),
+                         "krylov_iters": statistics.mean(s_.solve.iters for s_ in stats), "side": side})
+            prev = (ab[0].clone(), ab[1].clone(), g.clone(), keys)
+        return ctx, rows
+
+    # training data: window solutions along the trajectories of seeds 2 and 3
+    train = []
+
+    def keep(step, c, con, g, dev_before, sc):
+        if step % max(1, args.box_train_steps // 3) == 0:
+            tc = binding.Context()
+            tcon = tc.assemble(dev_before, sc.floor_z, sc.gravity, sc.dt, sc.delta, sc.mu, 3, sc.walls)
+            assert tcon.Nc == con.Nc
+            train.append((tc, g[:3 * con.Nc].clone()))
+        return None
+
+    t0 = time.perf_counter()
+    for seed in (2, 3):
+        c, _ = trajectory(seed, args.box_train_steps, keep)
+        c.close()
+    gn_all = torch.cat([t[0::3] for _, t in train])
+    out_scale = max(float(gn_all.mean()), 1e-6)
+    net = learned.WarmStartNet(11, scale, out_scale)
+    losses = []
+    for _ in range(args.box_train_epochs):
+        for c, t in train:
+            losses.append(net.train_step(c, t, 1e-3))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    # seed 1: the timed trajectory, with the QTT and learned-start comparisons beside it
+    def side(step, c, con, g, dev_before, sc):
+        out = {}
+        g3, l3, s3 = fresh_state(con)
+        c.pdip_init(s3, 1.0)
+        r = c.pdip_step(s3, qtt_opts(c), allow=ok)
+        out["qtt_reuse"] = {"refresh_ms": r.ms_refresh, "krylov_iters": r.solve.iters, "solve_ms": r.solve.ms}
+        if step % 25 == 0:
+            fc = binding.Context()
+            fcon = fc.assemble(dev_before, sc.floor_z, sc.gravity, sc.dt, sc.delta, sc.mu, 3, sc.walls)
+            g5, l5, s5 = fresh_state(fcon)
+            fc.pdip_init(s5, 1.0)
+            r5 = fc.pdip_step(s5, qtt_opts(fc), allow=ok)
+            out["qtt_scratch"] = {"refresh_ms": r5.ms_refresh, "krylov_iters": r5.solve.iters,
+                                  "solve_ms": r5.solve.ms}
+            fc.close()
+        if step % 10 == 0:
+            o = opts_for(c)
+            g4, l4, s4 = fresh_state(con)
+            c.pdip_init(s4, 1.0)
+            for _ in range(W):
+                c.pdip_step(s4, o, allow=ok)
+            cold = c.pdip_measure(s4)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.warm_start(c, s4, con.Nc, gn_min=1e-3 * out_scale)
+            e1.record(stream)
+            start = c.pdip_measure(s4)
+            for _ in range(W):
+                c.pdip_step(s4, o, allow=ok)
+            learned_end = c.pdip_measure(s4)
+            # control: the cold start scaled to the learned start's impulse floor
+            # (the targets are near zero, so the network's output is too)
+            c.pdip_init(s4, 1e-3 * out_scale)
+            for _ in range(W):
+                c.pdip_step(s4, o, allow=ok)
+            out["starts"] = {"cold": cold, "learned": learned_end, "learned_at_start": start,
+                             "cold_scaled_to_learned": c.pdip_measure(s4),
+                             "learned_start_ms": e0.elapsed_time(e1)}
+        return out
+
+    ctx, rows = trajectory(1, args.box_steps, side, timed=True)
+    ctx.close()
+    for c, _ in train:
+        c.close()
+    ms = [r["ms_assemble"] + r["ms_pdip_window"] + r["ms_advance"] for r in rows]
+    warm = [r for r in rows if r["step"] > 0]
+    reuse = [r["side"]["qtt_reuse"] for r in warm]
+    scratch = [r["side"]["qtt_scratch"] for r in rows if "qtt_scratch" in r["side"]]
+    starts = [dict(step=r["step"], warm=(r["eta"], r["r_dual"]), **r["side"]["starts"]) for r in rows
+              if "starts" in r["side"]]
+    steps_total = sum(ms) / 1e3
+    return {"scene": "box40 seed 1: 64 000 spheres, radius U[0.4, 0.6], walls x, y = 0, 40, floor z = 0",
+            "steps": len(rows), "pdip_iterations_per_step": W,
+            "ms_per_time_step": statistics.mean(ms), "time_steps_per_s": len(rows) / steps_total,
+            "pdip_steps_per_s": sum(r["pdip_ok"] for r in rows) / steps_total,
+            "newton_solves_per_s": sum(r["solves_converged"] for r in rows) / steps_total,
+            "ms_assemble": statistics.mean(r["ms_assemble"] for r in rows),
+            "ms_pdip_window": statistics.mean(r["ms_pdip_window"] for r in rows),
+            "ms_advance": statistics.mean(r["ms_advance"] for r in rows),
+            "contacts_first_last": [rows[0]["contacts"], rows[-1]["contacts"]],
+            "padded_unknowns": rows[0]["padded_unknowns"],
+            "persisting_mean": statistics.mean(r["persisting"] for r in warm) if warm else None,
+            "eta_r_dual_first_last": [[rows[0]["eta"], rows[0]["r_dual"]], [rows[-1]["eta"], rows[-1]["r_dual"]]],
+            "krylov_iters_per_solve": statistics.mean(r["krylov_iters"] for r in rows),
+            "qtt": {"refresh_ms_reusing_previous_step": statistics.mean(x["refresh_ms"] for x in reuse)
+                    if reuse else None,
+                    "krylov_iters_reusing": statistics.mean(x["krylov_iters"] for x in reuse) if reuse else None,
+                    "refresh_ms_from_scratch": statistics.mean(x["refresh_ms"] for x in scratch),
+                    "krylov_iters_from_scratch": statistics.mean(x["krylov_iters"] for x in scratch),
+                    "eps": args.qtt_eps, "rmax": args.qtt_rmax},
+            "learned": {"train": {"scenes": f"box40 seeds 2, 3, window solutions of steps 0..{args.box_train_steps - 1}",
+                                  "snapshots": len(train), "epochs": args.box_train_epochs,
+                                  "first_loss": losses[0] if losses else None,
+                                  "final_loss": losses[-1] if losses else None, "seconds": t_train,
+                                  "out_scale": out_scale},
+                        "eval": starts},
+            "l2": "flushed (512 MiB write) before every step",
+            "note": "the step time excludes the QTT and learned-start comparisons run beside it"}
+
+
 # ---------------------------------------------------------------------- oracle arm
 def oracle_data(scene):
     from oracle import contacts as oc, qp
@@ -1130,6 +1317,10 @@ def main():
     ap.add_argument("--ts-qtt", type=int, default=1, help="time-stepping leg: measure the QTT refresh reuse (0: skip)")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
     ap.add_argument("--learned-steps", type=int, default=300, help="training epochs of the learned leg (0: skip)")
+    ap.add_argument("--box-steps", type=int, default=100, help="time steps of the walled-box leg (0: skip)")
+    ap.add_argument("--box-window", type=int, default=20, help="walled-box leg: PDIP iterations per time step")
+    ap.add_argument("--box-train-steps", type=int, default=30, help="walled-box leg: steps of each training seed")
+    ap.add_argument("--box-train-epochs", type=int, default=100, help="walled-box leg: training epochs")
     ap.add_argument("--config-legs", type=int, default=1,
                     help="also run the 8^3 FP64, the columns PDIP-to-gap and the 20^3 FP64 QTT legs (0: skip)")
     ap.add_argument("--qtt-krylov", default="cg", choices=["bicgstab", "cg"],

@@ -74,6 +74,10 @@ typedef struct {
   double delta;             /* contact envelope: active iff gap Phi <= delta     */
   double mu;                /* friction coefficient of every contact             */
   int slots;                /* rows per contact in the padded layout: 3 or 4     */
+  int nwalls;               /* side walls, 0..4 (an extension for boxed scenes): */
+  int wall_axis[4];         /*   static planes x_axis = wall_offset, axis 0..2,  */
+  int wall_sign[4];         /*   the box on the side sign = +1 or -1             */
+  double wall_offset[4];
 } qp_scene;
 
 typedef struct {
@@ -91,8 +95,13 @@ typedef struct {
 } qp_contacts;
 
 /* Active set A(q, delta) (Sec. 2.2): every sphere pair with gap
- * Phi = |x_b - x_a| - r_a - r_b <= delta and every sphere with
- * Phi = z - floor_z - r <= delta.  Builds frames (normal from a to b; t1 =
+ * Phi = |x_b - x_a| - r_a - r_b <= delta, every sphere with
+ * Phi = z - floor_z - r <= delta, and every sphere with
+ * Phi = sign (x_axis - offset) - r <= delta against a side wall (normal
+ * sign e_axis, contact point offset + sign Phi/2 on that axis, the floor's
+ * rule); floor and walls are the static body M (ties in the order broken by
+ * plane: floor, then walls in their order); nwalls outside 0..4, an axis
+ * outside 0..2 or a sign other than +-1 is QP_INVALID_ARG.  Builds frames (normal from a to b; t1 =
  * normalize(n x e), e the axis minimising |n_e|; t2 = n x t1), contact points
  * p = x_a + n (r_a + Phi/2), arms, Morton keys (21 bits per axis over the
  * bounding box of the contact points), the ordered list, the body->contact

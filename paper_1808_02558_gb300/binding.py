@@ -34,7 +34,8 @@ class Scene(C.Structure):
     _fields_ = [("M", C.c_int), ("pos", C.c_void_p), ("vel", C.c_void_p), ("omega", C.c_void_p),
                 ("radius", C.c_void_p), ("inv_mass", C.c_void_p), ("inv_inertia", C.c_void_p),
                 ("floor_z", C.c_double), ("gravity", C.c_double * 3), ("dt", C.c_double), ("delta", C.c_double),
-                ("mu", C.c_double), ("slots", C.c_int)]
+                ("mu", C.c_double), ("slots", C.c_int), ("nwalls", C.c_int), ("wall_axis", C.c_int * 4),
+                ("wall_sign", C.c_int * 4), ("wall_offset", C.c_double * 4)]
 
 
 class Contacts(C.Structure):
@@ -251,12 +252,18 @@ class Context:
             pass
 
     # ------------------------------------------------------------- assembly
-    def assemble(self, scene_dev: dict, floor_z, gravity, dt, delta, mu, slots=3) -> Contacts:
-        """scene_dev: dict of device float64 tensors pos/vel/omega (3, M) SoA and radius/inv_mass/inv_inertia (M,)."""
+    def assemble(self, scene_dev: dict, floor_z, gravity, dt, delta, mu, slots=3, walls=()) -> Contacts:
+        """scene_dev: dict of device float64 tensors pos/vel/omega (3, M) SoA and radius/inv_mass/inv_inertia (M,);
+        walls: up to four side walls (axis, sign, offset)."""
         M = int(scene_dev["radius"].shape[0])
+        walls = list(walls)
+        ax = [int(w[0]) for w in walls] + [0] * (4 - len(walls))
+        sg = [int(w[1]) for w in walls] + [1] * (4 - len(walls))
+        off = [float(w[2]) for w in walls] + [0.0] * (4 - len(walls))
         sc = Scene(M, _ptr(scene_dev["pos"]), _ptr(scene_dev["vel"]), _ptr(scene_dev["omega"]),
                    _ptr(scene_dev["radius"]), _ptr(scene_dev["inv_mass"]), _ptr(scene_dev["inv_inertia"]),
-                   float(floor_z), (C.c_double * 3)(*gravity), float(dt), float(delta), float(mu), int(slots))
+                   float(floor_z), (C.c_double * 3)(*gravity), float(dt), float(delta), float(mu), int(slots),
+                   len(walls), (C.c_int * 4)(*ax[:4]), (C.c_int * 4)(*sg[:4]), (C.c_double * 4)(*off[:4]))
         out = Contacts()
         self._check(self.lib.ccp_assemble(self.h, C.byref(sc), C.byref(out)), "ccp_assemble")
         self.contacts = out

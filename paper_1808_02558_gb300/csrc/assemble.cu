@@ -127,8 +127,24 @@ __global__ void k_pos32(int M, const double* __restrict__ pos, const double* __r
                          (float)(pos[2 * (size_t)M + i] - g.lo[2]), (float)rad[i]);
 }
 
+// Side walls of a boxed scene: static planes x_axis = off with the box on the
+// side of sign (+1 / -1).
+struct Walls {
+  int n;
+  int axis[4];
+  int sign[4];
+  double off[4];
+};
+
+__device__ __forceinline__ double wall_gap(const double* pos, const double* rad, int M, int b, const Walls& wl,
+                                           int w) {
+  const double x = pos[(size_t)wl.axis[w] * M + b];
+  return wl.sign[w] > 0 ? dsub(dsub(x, wl.off[w]), rad[b]) : dsub(dsub(wl.off[w], x), rad[b]);
+}
+
 // Count (write == nullptr) or write the contacts of body a: partners b > a in
-// the 27 neighbouring cells, then the floor.  Written pairs of one body are in
+// the 27 neighbouring cells, then the floor, then the side walls (a wall's raw
+// first body is M + 1 + w until the contacts are ordered; then it is M).  Written pairs of one body are in
 // arbitrary order; the global order is fixed afterwards by sorting.
 // Each candidate is first tested in FP32 against an envelope widened by a bound
 // on the FP32 rounding (err: 4 x the largest coordinate error, plus a relative
@@ -136,9 +152,9 @@ __global__ void k_pos32(int M, const double* __restrict__ pos, const double* __r
 // is the exact one while most FP64 work (a narrow pipe on this part) is skipped.
 __global__ void k_pairs(int M, const double* __restrict__ pos, const double* __restrict__ rad, Grid g,
                         const int* __restrict__ cstart, const int* __restrict__ cend,
-                        const int* __restrict__ sbody, double delta, double floor_z, int* __restrict__ count,
-                        const int* __restrict__ offset, int* __restrict__ wa, int* __restrict__ wb,
-                        const float4* __restrict__ p32, float err) {
+                        const int* __restrict__ sbody, double delta, double floor_z, Walls wl,
+                        int* __restrict__ count, const int* __restrict__ offset, int* __restrict__ wa,
+                        int* __restrict__ wb, const float4* __restrict__ p32, float err) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= M) return;
   const float4 pa = p32[a];
@@ -187,12 +203,21 @@ __global__ void k_pairs(int M, const double* __restrict__ pos, const double* __r
     }
     ++k;
   }
+  for (int w = 0; w < wl.n; ++w) {
+    if (wall_gap(pos, rad, M, a, wl, w) <= delta) {
+      if (wa) {
+        wa[base + k] = M + 1 + w;
+        wb[base + k] = a;
+      }
+      ++k;
+    }
+  }
   if (count) count[a] = k;
 }
 
 // Gap, normal and contact point of every raw contact, plus the (a, b) sort key.
 __global__ void k_geom_raw(int n, int M, const double* __restrict__ pos, const double* __restrict__ rad,
-                           double floor_z, const int* __restrict__ wa, const int* __restrict__ wb,
+                           double floor_z, Walls wl, const int* __restrict__ wa, const int* __restrict__ wb,
                            double* __restrict__ phi, double* __restrict__ nrm, double* __restrict__ pt,
                            unsigned long long* __restrict__ abkey, int* __restrict__ idx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -208,6 +233,19 @@ __global__ void k_geom_raw(int n, int M, const double* __restrict__ pos, const d
     px = pos[b];
     py = pos[(size_t)M + b];
     pz = dadd(floor_z, dmul(ph, 0.5));
+  } else if (a > M) {
+    // side wall w: normal sign e_axis, point offset + sign Phi/2 on that axis
+    const int w = a - M - 1, ax = wl.axis[w];
+    ph = wall_gap(pos, rad, M, b, wl, w);
+    const double sn = wl.sign[w] > 0 ? 1.0 : -1.0;
+    const double hp = dmul(ph, 0.5);
+    const double pw = dadd(wl.off[w], wl.sign[w] > 0 ? hp : -hp);
+    nx = ax == 0 ? sn : 0.0;
+    ny = ax == 1 ? sn : 0.0;
+    nz = ax == 2 ? sn : 0.0;
+    px = ax == 0 ? pw : pos[b];
+    py = ax == 1 ? pw : pos[(size_t)M + b];
+    pz = ax == 2 ? pw : pos[2 * (size_t)M + b];
   } else {
     double xa = pos[a], ya = pos[(size_t)M + a], za = pos[2 * (size_t)M + a];
     double dx = dsub(pos[b], xa);
@@ -273,6 +311,7 @@ __global__ void k_gather(int n, int M, const int* __restrict__ perm2, const int*
   if (c >= n) return;
   int j = perm1[perm2[c]];
   int a = wa[j], b = wb[j];
+  if (a > M) a = M;  // every static plane (floor or wall) is body M
   ca[c] = a;
   cb[c] = b;
   phi[c] = phi_raw[j];
@@ -406,6 +445,16 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   QP_REQUIRE(s->dt > 0 && s->delta >= 0, QP_INVALID_ARG, "ccp_assemble: dt > 0 and delta >= 0 required");
   QP_REQUIRE(s->pos && s->vel && s->omega && s->radius && s->inv_mass && s->inv_inertia, QP_INVALID_ARG,
              "ccp_assemble: null scene array");
+  QP_REQUIRE(s->nwalls >= 0 && s->nwalls <= 4, QP_INVALID_ARG, "ccp_assemble: nwalls must be 0..4");
+  Walls wl{};
+  wl.n = s->nwalls;
+  for (int w = 0; w < s->nwalls; ++w) {
+    QP_REQUIRE(s->wall_axis[w] >= 0 && s->wall_axis[w] <= 2 && (s->wall_sign[w] == 1 || s->wall_sign[w] == -1),
+               QP_INVALID_ARG, "ccp_assemble: wall axis must be 0..2 and sign +-1");
+    wl.axis[w] = s->wall_axis[w];
+    wl.sign[w] = s->wall_sign[w];
+    wl.off[w] = s->wall_offset[w];
+  }
   QP_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = c->stream;
   const int M = s->M;
@@ -466,7 +515,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   for (int a2 = 0; a2 < 3; ++a2) ext = std::max(ext, box.hi[a2] - box.lo[a2]);
   const float perr = (float)(4.0 * (ext + 2.0 * box.rmax + s->delta + 1.0) * 6.0e-8) + 1e-30f;
   k_pos32<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, p32);
-  k_pairs<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, cstart, cend, body_s, s->delta, s->floor_z,
+  k_pairs<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, cstart, cend, body_s, s->delta, s->floor_z, wl,
                                           count, nullptr, nullptr, nullptr, p32, perr);
   QP_CUDA(cudaGetLastError());
   tmp_bytes = 0;
@@ -541,14 +590,15 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
                                               c->inv_I.as<double>(), c->inv_m32.as<float>(), c->inv_I32.as<float>());
   int* bptr = c->bptr.as<int>();
   if (Nc > 0) {
-    k_pairs<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, cstart, cend, body_s, s->delta, s->floor_z,
+    k_pairs<<<ceil_div(M, TB), TB, 0, st>>>(M, s->pos, s->radius, g, cstart, cend, body_s, s->delta, s->floor_z, wl,
                                             nullptr, offset, wa, wb, p32, perr);
-    k_geom_raw<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, M, s->pos, s->radius, s->floor_z, wa, wb, phi_raw, nrm_raw,
+    k_geom_raw<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, M, s->pos, s->radius, s->floor_z, wl, wa, wb, phi_raw, nrm_raw,
                                                 pt_raw, k1, i0);
     QP_CUDA(cudaGetLastError());
     // 4. order: sort by (a, b), then stable sort by Morton key -> (key, a, b)
     int abbits = 1;
-    while (abbits < 64 && (1ull << abbits) <= (unsigned long long)(M + 1) * (unsigned long long)(M + 1)) ++abbits;
+    // raw first bodies reach M + 4 (walls): keys below (M + 5)(M + 1)
+    while (abbits < 64 && (1ull << abbits) <= (unsigned long long)(M + 5) * (unsigned long long)(M + 1)) ++abbits;
     tmp_bytes = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k1, k1s, i0, i1, Nc, 0, abbits, st);
     size_t t2 = 0;

@@ -25,7 +25,8 @@ def scene_to_device(scene, device="cuda") -> dict:
 def assemble(ctx: binding.Context, scene, slots: int = 3, device="cuda"):
     """Upload `scene` and build its contacts; returns (device scene dict, contacts view)."""
     dev = scene_to_device(scene, device)
-    con = ctx.assemble(dev, scene.floor_z, scene.gravity, scene.dt, scene.delta, scene.mu, slots)
+    con = ctx.assemble(dev, scene.floor_z, scene.gravity, scene.dt, scene.delta, scene.mu, slots,
+                       getattr(scene, "walls", ()))
     return dev, con
 
 

@@ -139,24 +139,32 @@ def column_scene(nx: int, height: int, seed: int, *, lateral: float = 1.03, spac
                  radius=np.full(M, 0.5), mu=mu, dt=dt, delta=0.0, seed=seed)
 
 
-def box_scene(seed: int, *, n: int = 40, layers: int = 40, spacing: float = 1.0, lift: float = 2.0,
-              jitter: float = 0.01, vel_sigma: float = 0.1, mu: float = 0.5, dt: float = 1e-3,
-              delta: float = 0.21, name: str | None = None) -> Scene:
-    """Polydisperse spheres (radius U[0.4, 0.6], density 1) in a walled box of
-    n x n x 2n: an n x n x layers jittered lattice, `spacing` apart across and
-    `lift` apart in height (the layers fall onto each other under gravity),
-    velocities N(0, vel_sigma^2), side walls at x, y = -spacing/2 and
-    (n - 1/2) spacing, the floor at z = 0 under the lowest layer's centres at 0.5.
-    Body id = i + n*j + n*n*k."""
+def box_scene(seed: int, *, n: int = 40, layers: int = 40, side: float | None = None, lift: float = 2.0,
+              stagger: float = 0.8, clear: float = 0.61, jitter: float = 0.01, vel_sigma: float = 0.1,
+              mu: float = 0.5, dt: float = 1e-3, delta: float = 0.25, name: str | None = None) -> Scene:
+    """Polydisperse spheres (radius U[0.4, 0.6], density 1) falling in a walled
+    box of side x side (2 side high; side = n unless given): an n x n x layers
+    lattice spread evenly across the box with `clear` (above the largest radius
+    plus the jitter) between the outer centres and the walls and between the
+    lowest centres and the floor, layers `lift` apart, every other column (i + j
+    odd) raised by `stagger` so that neighbours across are about 1.25 apart and
+    no two spheres overlap at n = 40.  Positions jittered U(+-jitter) per
+    coordinate, velocities N(0, vel_sigma^2); walls x, y = 0 and side, floor
+    z = 0.  Body id = i + n*j + n*n*k."""
+    if n < 2:
+        raise ValueError("box_scene needs n >= 2")
+    side = float(n) if side is None else float(side)
+    spacing = (side - 2.0 * clear) / (n - 1)
     M = n * n * layers
     k, j, i = np.meshgrid(np.arange(layers), np.arange(n), np.arange(n), indexing="ij")
-    site = np.stack([i.ravel() * spacing, j.ravel() * spacing, k.ravel() * lift], axis=1).astype(np.float64)
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    site = np.stack([clear + i * spacing, clear + j * spacing, clear + k * lift + stagger * ((i + j) % 2)],
+                    axis=1).astype(np.float64)
     jit = (2.0 * splitmix64_uniform(seed, 1, 3 * M) - 1.0).reshape(M, 3) * jitter
-    pos = site + np.array([0.0, 0.0, 0.5]) + jit
+    pos = site + jit
     vel = normal_vector(seed, 2, 3 * M, vel_sigma).reshape(M, 3)
     radius = 0.4 + 0.2 * splitmix64_uniform(seed, 3, M)
-    lo, hi = -0.5 * spacing, (n - 0.5) * spacing
-    walls = ((0, 1, lo), (0, -1, hi), (1, 1, lo), (1, -1, hi))
+    walls = ((0, 1, 0.0), (0, -1, side), (1, 1, 0.0), (1, -1, side))
     return Scene(name=name or f"box{n}-s{seed}", pos=pos, vel=vel, omega=np.zeros((M, 3)), radius=radius, mu=mu,
                  dt=dt, delta=delta, seed=seed, walls=walls)
 

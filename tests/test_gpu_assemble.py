@@ -5,7 +5,7 @@ import torch
 
 from gpu_common import Problem, to_np
 from paper_1808_02558_gb300 import binding, workload
-from synth import Scene, lattice_scene, scene_for
+from synth import Scene, box_scene, lattice_scene, scene_for
 
 pytestmark = pytest.mark.gpu
 
@@ -61,3 +61,33 @@ def test_assemble_edge_cases(ctx):
     check_bitexact(Problem(ctx, two))
     # ragged lattice (not a power of two) with a large envelope
     check_bitexact(Problem(ctx, lattice_scene(5, 9, polydisperse=True, delta=0.45)))
+
+
+def test_assemble_walled_box_small(ctx):
+    # 6 x 6 x 3 box: spheres against both walls of each side axis, in the
+    # corners against two walls and the floor at once (ties ordered by plane)
+    check_bitexact(Problem(ctx, box_scene(1, n=6, layers=3)))
+    check_bitexact(Problem(ctx, box_scene(2, n=5, layers=2, lift=1.0), 4))
+
+
+def test_assemble_walled_box_full(ctx):
+    # 64 000 spheres in the 40 x 40 x 80 box
+    pb = Problem(ctx, scene_for("box40", 1))
+    check_bitexact(pb)
+    a, b = to_np(workload.view(pb.con, "body_a")), to_np(workload.view(pb.con, "body_b"))
+    planes = a == pb.scene.M
+    # floor contacts have normal +e_z, wall contacts normal +-e_x or +-e_y
+    n = to_np(workload.view(pb.con, "frame")).reshape(9, -1)[0:3].T[planes]
+    assert np.all(np.abs(n).max(axis=1) == 1.0)
+    assert (np.abs(n[:, 0]) == 1.0).sum() > 0 and (np.abs(n[:, 1]) == 1.0).sum() > 0
+
+
+def test_assemble_wall_arguments(ctx):
+    s = box_scene(1, n=3, layers=1)
+    c = binding.Context()
+    dev = workload.scene_to_device(s, "cuda")
+    for walls in [((0, 1, 0.0),) * 5, ((3, 1, 0.0),), ((0, 0, 0.0),), ((1, 2, 0.0),)]:
+        with pytest.raises(binding.QPError) as e:
+            c.assemble(dev, s.floor_z, s.gravity, s.dt, s.delta, s.mu, 3, walls)
+        assert e.value.code == binding.QP_INVALID_ARG
+    c.close()

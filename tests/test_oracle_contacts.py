@@ -130,9 +130,23 @@ def test_box_scene_counts_and_order():
     c = oc.detect(s)
     stat = c.a == s.M
     n, layers = 6, 4
-    assert int(stat.sum()) == n * n + 4 * n * layers
+    # the floor under the lower half of the checkerboard of the bottom layer
+    assert int(stat.sum()) == n * n // 2 + 4 * n * layers
     floor = stat & (c.n[:, 2] == 1.0)
-    assert int(floor.sum()) == n * n
+    assert int(floor.sum()) == n * n // 2
     pairs = oc.candidate_pairs_bruteforce(s.pos, s.radius, s.delta)
     assert int((~stat).sum()) == len(pairs)
     assert np.all(np.diff(c.key.astype(np.float64)) >= 0)
+
+
+def test_box40_starts_without_overlap():
+    """The 64 000-sphere box starts with every gap (pairs, floor, walls) >= 0:
+    the spheres fall, nothing is pushed apart by an initial overlap."""
+    from synth import scene_for
+
+    s = scene_for("box40", 1)
+    c = oc.detect(s)
+    assert s.M == 64000 and c.Nc > 50000
+    assert c.phi.min() >= 0.0
+    side = s.walls[1][2]
+    assert side == 40.0 and s.pos[:, 2].max() < 2.0 * side
