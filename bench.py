@@ -413,6 +413,7 @@ def run_ours(args):
     if learned_out is not None:
         learned_out["network_at_bench_scale"] = mpnn_scale_leg(binding, workload, scene, flush, stream)
     box_out = box_leg(args, binding, workload, flush, stream) if args.box_steps > 0 else None
+    dense_out = qtt_dense_leg(binding, flush, stream) if args.qtt_dense else None
     configs_out = None
     if args.config_legs:
         cpu_ok = rank == 0 and not args.no_cpu_baseline
@@ -454,6 +455,7 @@ def run_ours(args):
         "learned_warm_start": learned_out,
         "configs": configs_out,
         "box_time_stepping": box_out,
+        "qtt_apply_rank64": dense_out,
     }
     if rank == 0 and not args.no_cpu_baseline:
         its = gpu_window_iterates(ctx, st, gamma, lam, opts, args.window, ok, Nc)
@@ -947,6 +949,55 @@ def time_stepping_leg(args, binding, workload, scene, opts, ok, flush, stream):
             "note": "Jacobi-PCG windows; warm start = previous impulses of persisting pairs moved into the cone"}
 
 
+def qtt_dense_leg(binding, flush, stream, reps=10):
+    """QTT apply at rank cap 64 (d = 20: 2^20 unknowns, ranks min(64, 4^k,
+    4^(d-k)), BF16 cores, FP32 vectors), the profile of a Schur inverse
+    compressed at eps 1e-3, r <= 64: the CUDA-core steps against the tensor-core
+    steps (tcgen05, split TF32) of the dense cores.  Bytes: each core's pass
+    reads r_k N and writes r_{k-1} N FP32 values; flops 4 r_{k-1} r_k N per core
+    (N/2 column items, each a (2 r_{k-1}) x (2 r_k) matrix-vector product)."""
+    import numpy as np
+    import torch
+
+    d, N = 20, 1 << 20
+    ranks = [min(64, 4 ** min(k, d - k)) for k in range(d + 1)]
+    rng = np.random.default_rng(7)
+    cores = [rng.standard_normal((ranks[k], 4, ranks[k + 1])) / np.sqrt(2 * ranks[k + 1]) for k in range(d)]
+    ctx = binding.Context()
+    A = ctx.qtt_from_cores(cores)
+    x = torch.randn(N, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    nbytes = sum((ranks[k] + ranks[k + 1]) * N * 4 for k in range(d))
+    flops = sum(4 * ranks[k] * ranks[k + 1] * N for k in range(d))
+    dense = [k + 1 for k in range(d) if ranks[k] * ranks[k + 1] >= 512]
+    dense_bytes = sum((ranks[k - 1] + ranks[k]) * N * 4 for k in dense)
+    out = {"d": d, "ranks": ranks, "core_dtype": "bf16", "bytes": nbytes, "flops": flops,
+           "tensor_core_cores": len(dense), "tensor_core_bytes": dense_bytes}
+    hbm, src = peaks()
+    for mode, name in ((0, "cuda_cores"), (1, "tensor_cores")):
+        ctx.qtt_set_tensor_cores(mode)
+        for _ in range(3):
+            ctx.qtt_apply(A, x, y, binding.QP_BF16, binding.QP_F32)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.qtt_apply(A, x, y, binding.QP_BF16, binding.QP_F32)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms) / 1e3
+        out[name] = {"us": t * 1e6, "gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / hbm,
+                     "tflops": flops / t / 1e12, "fp32_alu_frac": flops / t / 1e12 / FP32_ALU_TFLOPS}
+    out["speedup"] = out["cuda_cores"]["us"] / out["tensor_cores"]["us"]
+    out["peak_source"] = src
+    A.free()
+    ctx.close()
+    return out
+
+
 def box_leg(args, binding, workload, flush, stream):
     """Time stepping of 64 000 polydisperse spheres falling in the walled 40 x 40
     x 80 box (Sec. 2.3), args.box_steps steps of seed 1.  A step: assemble (pairs,
@@ -1318,6 +1369,7 @@ def main():
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched leg (0: skip)")
     ap.add_argument("--learned-steps", type=int, default=300, help="training epochs of the learned leg (0: skip)")
     ap.add_argument("--box-steps", type=int, default=100, help="time steps of the walled-box leg (0: skip)")
+    ap.add_argument("--qtt-dense", type=int, default=1, help="time the rank-64 QTT apply, CUDA vs tensor cores (0: skip)")
     ap.add_argument("--box-window", type=int, default=20, help="walled-box leg: PDIP iterations per time step")
     ap.add_argument("--box-train-steps", type=int, default=30, help="walled-box leg: steps of each training seed")
     ap.add_argument("--box-train-epochs", type=int, default=100, help="walled-box leg: training epochs")

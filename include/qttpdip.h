@@ -370,6 +370,19 @@ int qtt_copy_cores_to_host(qtt_t A, double* cores_host);
  * (float[2^d]); QP_F64 vectors require QP_F64 cores.                        */
 int qtt_apply(qp_ctx_t ctx, qtt_t A, const void* x, void* y, qp_dtype core_dtype, qp_dtype vec_dtype);
 
+/* Which cores qtt_apply contracts on the tensor cores (tcgen05, TF32 products
+ * with the FP32 vector split into a TF32 part and a remainder; F32 cores split
+ * the same way).  Only FP32 vectors with BF16 or F32 cores, d >= 8, and cores
+ * with r_{k-1}, r_k <= 64 qualify.  The result is good to about 1e-5 of the
+ * largest entry (the CUDA-core steps: about 4e-7).  mode 0: none; 1 (the
+ * default): BF16 cores with r_{k-1} r_k >= 512, where the contraction is
+ * dense enough to pay and the cores' own rounding (2^-9) dominates; 2: every
+ * core that qualifies, F32 cores included.  Applies to later qtt_apply calls
+ * on this context; the Krylov solvers' preconditioner keeps its CUDA-core
+ * step.  QP_INVALID_ARG for another mode; a tensor-core step whose wait
+ * expires makes qtt_apply return QP_TIMEOUT.                                */
+int qtt_set_tensor_cores(qp_ctx_t ctx, int mode);
+
 /* TT rounding: right-to-left QR orthogonalisation then left-to-right
  * truncated SVD in FP64, keeping per split the smallest rank with discarded
  * norm <= eps ||A||_F / sqrt(d-1), capped at rmax (Sec. 3.1 truncation rule,

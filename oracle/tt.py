@@ -112,6 +112,25 @@ def qtt_matvec(cores: list, x: np.ndarray) -> np.ndarray:
     return Z.reshape(-1)
 
 
+def qtt_matvec_kron_entries(cores: list, v: np.ndarray, rows) -> np.ndarray:
+    """Entries y[rows] of y = A_TT x for the Kronecker-product vector
+    x = v_1 (x) v_2 (x) ... (x) v_d (v of shape (d, 2), v_1 on the most
+    significant bit).  The QTT matrix acts mode by mode (Sec. 3.2), so for such
+    an x the column bits separate and y(i) = prod_k M_k(i_k), a product of the
+    r_{k-1} x r_k matrices M_k(i_k)[a, b] = sum_j G_k(a, i_k, j, b) v_k[j]:
+    O(d r^2) work per entry, at any d."""
+    d = len(cores)
+    Ms = [np.einsum("aijb,j->iab", G.reshape(G.shape[0], 2, 2, G.shape[2]), np.asarray(v[k], dtype=np.float64))
+          for k, G in enumerate(cores)]
+    out = np.empty(len(rows))
+    for n, i in enumerate(rows):
+        acc = np.ones((1, 1))
+        for k in range(d):
+            acc = acc @ Ms[k][(int(i) >> (d - 1 - k)) & 1]
+        out[n] = acc[0, 0]
+    return out
+
+
 def tt_add(A: list, B: list) -> list:
     """A + B as a TT of ranks r_A + r_B (block cores)."""
     d = len(A)

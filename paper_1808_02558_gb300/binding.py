@@ -26,7 +26,8 @@ QTT_NOALLOC_MAX_VALUES = 1 << 22
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
            "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "newton_batch_plan", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
            "ccp_advance", "qp_selftest_barrier", "mpnn_forward", "mpnn_grad", "mpnn_adam", "mpnn_warm_start", "qtt_from_host",
-           "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_round",
+           "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_set_tensor_cores",
+           "qtt_round",
            "qtt_compress", "qtt_inverse", "qtt_apply_f32_noalloc"]
 
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         "qtt_get_ranks": (i, [vp, C.POINTER(i)]),
         "qtt_copy_cores_to_host": (i, [vp, C.POINTER(d)]),
         "qtt_apply": (i, [vp, vp, vp, vp, i, i]),
+        "qtt_set_tensor_cores": (i, [vp, i]),
         "qtt_round": (i, [vp, vp, d, i, C.POINTER(vp)]),
         "qtt_compress": (i, [vp, C.POINTER(State), d, i, C.POINTER(vp)]),
         "qtt_inverse": (i, [vp, vp, d, i, i, vp, C.POINTER(vp)]),
@@ -377,6 +379,10 @@ class Context:
 
     def qtt_apply(self, A: QTT, x, y, core_dtype=QP_F64, vec_dtype=QP_F64):
         self._check(self.lib.qtt_apply(self.h, A.h, _ptr(x), _ptr(y), core_dtype, vec_dtype), "qtt_apply")
+
+    def qtt_set_tensor_cores(self, mode: int):
+        """0: CUDA-core steps only; 1: tensor cores for dense cores (default); 2: every core that qualifies."""
+        self._check(self.lib.qtt_set_tensor_cores(self.h, int(mode)), "qtt_set_tensor_cores")
 
     def qtt_round(self, A: QTT, eps: float, rmax: int = 1 << 30) -> QTT:
         h = C.c_void_p()

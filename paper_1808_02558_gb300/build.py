@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libqttpdip.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 SOURCES = ["ctx.cu", "assemble.cu", "newton.cu", "timestep.cu", "qtt.cu", "qtt_linalg.cu", "qtt_inverse.cu",
-           "qtt_static.cu", "mpnn.cu"]
+           "qtt_static.cu", "qtt_tc.cu", "mpnn.cu"]
 
 
 def nvcc() -> str:

@@ -107,7 +107,9 @@ struct qp_ctx {
   qp::Buf apart_nb, apart_bodies, apart_cl;
   qp::Buf fused_pool;
   qp::Buf mp_act, mp_w, mp_grad, mp_sum;  // learned warm start: activations, BF16 weights, scratch
-  qp::Buf batch64, batch32, batch_table;  // batched solves: per-scene vectors; table (first context)  // records of the fused pipelined solver (never shared with the classic solver)
+  qp::Buf batch64, batch32, batch_table;  // batched solves: per-scene vectors; table (first context)
+  qp::Buf tc_err;  // error flag of the tensor-core QTT step
+  int qtt_tc_mode = 1;  // tensor-core QTT steps: 0 never, 1 dense cores, 2 every core that fits
 };
 
 namespace qp {
@@ -141,6 +143,13 @@ void launch_schur_blocks(qp_ctx* c, const double* gamma, const double* lambda);
 void launch_apply64(qp_ctx* c, const double* x, double* y, bool with_H);
 void launch_apply32(qp_ctx* c, const float* x, float* y, bool with_H);
 void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype core_dt, qp_dtype vec_dt);
+// tensor-core QTT step (qtt_tc.cu): FP32 vectors, cores with r_{k-1}, r_k <= 64;
+// in the automatic mode only BF16 cores with r_{k-1} r_k >= QTT_TC_MIN_RR
+struct QttDev;
+constexpr int QTT_TC_MIN_RR = 512;
+bool qtt_tc_eligible(const qp_ctx* c, const QttDev& q, int k, qp_dtype core_dt);
+void launch_qtt_step_tc(qp_ctx* c, const QttDev& q, int k, const float* in, float* out, qp_dtype core_dt);
+int* qtt_tc_flag(qp_ctx* c);
 void qtt_prepare_copies(qp_ctx* c, qp_qtt* A, qp_dtype core_dt);
 qp_qtt* qtt_alloc(qp_ctx* c, int d, const std::vector<int>& ranks);
 size_t qtt_work_bytes(qp_qtt* A, qp_dtype core_dt);

@@ -16,6 +16,22 @@
 #include "tc.cuh"
 
 namespace qp {
+
+// The driver's tensor-map encoder, looked up once (shared with qtt_tc.cu).
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  QP_REQUIRE(fn != nullptr, QP_CUDA_ERROR, "cuTensorMapEncodeTiled is not available");
+  return fn;
+}
+
 namespace {
 
 constexpr int MF = 8, MW = 64, MO = 3, ML = 3;
@@ -404,19 +420,6 @@ inline int blocks_for(long long n, int per = 256, int cap = 152 * 32) {
 }
 
 // ---- host side of the tensor-core GEMM
-PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  QP_REQUIRE(fn != nullptr, QP_CUDA_ERROR, "cuTensorMapEncodeTiled is not available");
-  return fn;
-}
 
 // Row-major FP32 matrix [rows][64], boxes of 128 rows x 32 columns (128 bytes
 // wide, the 128-byte swizzle); rows past the end read as zeros.

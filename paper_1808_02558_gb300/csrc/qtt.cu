@@ -134,17 +134,33 @@ void launch_qtt_apply(qp_ctx* c, qp_qtt* A, const void* x, void* y, qp_dtype cdt
   void* w1 = c->scratch[6].ensure((size_t)N * q.rmax * es);
   const void* in = x;
   int pass = 0;
+  // tensor-core steps for the dense cores (FP32 vectors, BF16 or F32 cores);
+  // when every core that fits goes there, no two cores are fused into one pass
+  const bool tc_ok = vdt == QP_F32 && cdt != QP_F64;
+  const bool tc_all = tc_ok && c->qtt_tc_mode == 2 && A->d >= 8;
+  bool used_tc = false;
   for (int k = A->d; k >= 1; ++pass) {
-    const int bound = vdt == QP_F64 ? 0 : qtt_fuse_bound<float>(q, k, QTT_GQ);
+    const bool tcs = tc_ok && qtt_tc_eligible(c, q, k, cdt);
+    const int bound = (vdt == QP_F64 || tcs || tc_all) ? 0 : qtt_fuse_bound<float>(q, k, QTT_GQ);
     const int next = bound ? k - 2 : k - 1;
     void* out = (next == 0) ? y : ((pass & 1) ? w1 : w0);
-    if (vdt == QP_F64) launch_step<double, double, double>(c, q, k, in, out, bound, N);
+    if (tcs) {
+      if (!used_tc) QP_CUDA(cudaMemsetAsync(qtt_tc_flag(c), 0, sizeof(int), c->stream));
+      used_tc = true;
+      launch_qtt_step_tc(c, q, k, static_cast<const float*>(in), static_cast<float*>(out), cdt);
+    } else if (vdt == QP_F64) launch_step<double, double, double>(c, q, k, in, out, bound, N);
     else if (cdt == QP_F32) launch_step<float, float, float>(c, q, k, in, out, bound, N);
     else if (cdt == QP_BF16) launch_step<float, float, __nv_bfloat16>(c, q, k, in, out, bound, N);
     else launch_step<float, float, double>(c, q, k, in, out, bound, N);
     QP_CUDA(cudaGetLastError());
     in = out;
     k = next;
+  }
+  if (used_tc) {
+    int h = 0;
+    QP_CUDA(cudaMemcpyAsync(&h, qtt_tc_flag(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    QP_CUDA(cudaStreamSynchronize(c->stream));
+    QP_REQUIRE(h == 0, QP_TIMEOUT, "qtt_apply: a tensor-core step's wait expired");
   }
 }
 

@@ -94,6 +94,76 @@ def test_apply_full_size_d20(ctx):
     assert_close(to_np(y32), want32, 5e-4, floor_rel=1e-2, what="FP32 apply, d = 20")
 
 
+# ---------------------------------------------------------------- tensor-core steps
+def capped_cores(d, r, seed):
+    """Ranks min(r, 4^k, 4^(d-k)): the profile of a compressed Schur matrix's
+    inverse at rank cap r."""
+    rng = np.random.default_rng(seed)
+    ranks = [min(r, 4 ** min(k, d - k)) for k in range(d + 1)]
+    return [rng.standard_normal((ranks[k], 4, ranks[k + 1])) / np.sqrt(2 * ranks[k + 1]) for k in range(d)]
+
+
+# rank caps that pad K (2 r_k not a multiple of 32) and M (2 r_{k-1} < 128);
+# d = 8 has cores whose column items span several J' per tile (2^(d-k) < 32)
+@pytest.mark.parametrize("d,r", [(8, 64), (10, 33), (12, 64), (14, 40)])
+def test_apply_tensor_core_steps(d, r):
+    c = binding.Context()
+    cores = capped_cores(d, r, 100 + d)
+    A = c.qtt_from_cores(cores)
+    x32 = dev(np.random.default_rng(d).standard_normal(1 << d)).float()
+    xin = to_np(x32).astype(np.float64)
+    want = {binding.QP_F32: tt.qtt_matvec(cores, xin),
+            binding.QP_BF16: tt.qtt_matvec([bf16_round(g) for g in cores], xin)}
+    for cdt, name in ((binding.QP_BF16, "BF16"), (binding.QP_F32, "F32")):
+        got = {}
+        for mode in (0, 1, 2):
+            c.qtt_set_tensor_cores(mode)
+            y = torch.full_like(x32, float("nan"))
+            c.qtt_apply(A, x32, y, cdt, binding.QP_F32)
+            got[mode] = to_np(y).astype(np.float64)
+            assert_close(got[mode], want[cdt], 2e-4, floor_rel=1e-2, what=f"{name} cores, tensor-core mode {mode}")
+        # the split-TF32 products stay near FP32 accuracy: the largest error
+        # relative to the largest entry is ~3e-6 (BF16 cores) to ~1.2e-5 (F32
+        # cores) on the tensor cores, whose accumulator rounds more coarsely
+        # than an FMA chain, against ~4e-7 on the CUDA cores: far below TF32's
+        # 2^-11 ~ 5e-4 and the BF16 cores' 2^-9
+        scale = np.abs(want[cdt]).max()
+        e = {m: np.abs(got[m] - want[cdt]).max() / scale for m in got}
+        assert e[0] <= 2e-6 and max(e.values()) <= 4e-5, (name, e)
+    with pytest.raises(binding.QPError) as e:
+        c.qtt_set_tensor_cores(3)
+    assert e.value.code == binding.QP_INVALID_ARG
+    A.free()
+    c.close()
+
+
+def test_apply_tensor_core_full_size_d20():
+    """d = 20 (2^20 unknowns) at rank cap 64, BF16 cores, a Kronecker-product x:
+    4096 sampled entries against the oracle's per-entry product."""
+    c = binding.Context()
+    d = 20
+    cores = [bf16_round(g) for g in capped_cores(d, 64, 7)]
+    A = c.qtt_from_cores(cores)
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal((d, 2))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    x = v[0]
+    for k in range(1, d):
+        x = np.kron(x, v[k])
+    x32 = dev(x).float()
+    rows = np.sort(rng.choice(1 << d, 4096, replace=False))
+    want = tt.qtt_matvec_kron_entries(cores, v, rows)
+    for mode in (1, 0):
+        c.qtt_set_tensor_cores(mode)
+        y = torch.full_like(x32, float("nan"))
+        c.qtt_apply(A, x32, y, binding.QP_BF16, binding.QP_F32)
+        yn = to_np(y)
+        assert np.isfinite(yn).all()
+        assert_close(yn[rows].astype(np.float64), want, 5e-4, floor_rel=1e-2, what=f"d = 20, rank 64, mode {mode}")
+    A.free()
+    c.close()
+
+
 # ---------------------------------------------------------------- rounding (Sec. 3.1)
 def test_round_sum_recovers_ranks(ctx):
     rng = np.random.default_rng(7)

@@ -131,3 +131,23 @@ def test_inverse_reference_on_spd_matrix():
     T = 2.5 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
     X = tt.qtt_inverse_dense(T, 1e-10)
     assert np.allclose(tt.qtt_matrix(X) @ T, np.eye(n), atol=1e-8)
+
+
+def test_kron_entries_match_the_matvec():
+    """Entries of A_TT (v_1 x ... x v_d) from the per-mode factorisation equal
+    the full one-core-at-a-time contraction (itself pinned against A @ x)."""
+    rng = np.random.default_rng(7)
+    d = 7
+    ranks = [1, 3, 5, 6, 4, 5, 2, 1]
+    cores = [rng.standard_normal((ranks[k], 4, ranks[k + 1])) for k in range(d)]
+    v = rng.standard_normal((d, 2))
+    x = v[0]
+    for k in range(1, d):
+        x = np.kron(x, v[k])
+    want = tt.qtt_matvec(cores, x)
+    rows = np.arange(1 << d)
+    got = tt.qtt_matvec_kron_entries(cores, v, rows)
+    assert np.allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    # a transposed core (i and j swapped) changes the result
+    bad = [c.reshape(c.shape[0], 2, 2, c.shape[2]).transpose(0, 2, 1, 3).reshape(c.shape) for c in cores]
+    assert not np.allclose(tt.qtt_matvec_kron_entries(bad, v, rows), want, rtol=0, atol=1e-6 * np.abs(want).max())
