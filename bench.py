@@ -864,6 +864,39 @@ def batched_leg(args, binding, workload):
            "roofline": {"kernel": "k_pcg_batched", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                         "frac": ach / hbm, "peak_source": src, "bytes": nbytes,
                         "time": "device time of the launch (events)"}}
+    # every scene with its own QTT preconditioner: the inverse of its Jacobi-scaled
+    # Schur matrix at the paper's operating point (eps 1e-2, r <= 10), BF16 cores,
+    # the tile shapes from the measured table
+    t0 = time.perf_counter()
+    X = []
+    for c, st in zip(ctxs, states):
+        S_tt = c.qtt_compress(st, 1e-2, 10)
+        X.append(c.qtt_inverse(S_tt, 1e-2, 10, sweeps=2))
+        S_tt.free()
+    torch.cuda.synchronize()
+    t_refresh = time.perf_counter() - t0
+    qkw = dict(kw, precond=X, core_dtype=binding.QP_BF16, allow=(binding.QP_NOT_CONVERGED, binding.QP_BREAKDOWN))
+    qs, qused = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=0, **qkw)
+    t_q = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qs, qused = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=qused, **qkw)
+        t_q.append(time.perf_counter() - t0)
+    fixed = {}
+    for tile in (1, 2):
+        fs, _ = binding.newton_solve_batched(ctxs, states, rhs, dx, block_threads=qused, qtt_tile=tile, **qkw)
+        fixed[f"tile_{tile}_device_ms"] = fs[0].ms
+    out["qtt"] = {"eps": 1e-2, "rmax": 10, "core_dtype": "bf16", "block_threads": qused,
+                  "tiles_measured": ctxs[0].batch_qtt_tiles(qused), "batched_ms": statistics.median(t_q) * 1e3,
+                  "batched_device_ms": qs[0].ms, "batched_solves_per_s": n / statistics.median(t_q),
+                  "factor_vs_jacobi_batched": tb / statistics.median(t_q),
+                  "iters_mean": statistics.mean(s.iters for s in qs),
+                  "converged": sum(1 for s in qs if s.status == binding.QP_OK),
+                  "max_rel_res": max(s.rel_res for s in qs), "refresh_s_all_scenes": t_refresh, **fixed,
+                  "note": "tiles_measured: column items per thread for input ranks <= 4, <= 8, <= 16, above"}
+    for x in X:
+        x.free()
     for c in ctxs:
         c.close()
     return out
@@ -1053,10 +1086,10 @@ def box_leg(args, binding, workload, flush, stream):
             if prev is None:
                 ctx.pdip_init(st, 1.0)
             else:
-                ctx.pdip_init_warm(st, prev[0], prev[1], prev[2], 3)
+                ctx.pdip_init_warm(st, prev[0], prev[1], prev[2], 3, prev_plane=prev[4])
             stats = [ctx.pdip_step(st, opts, allow=ok) for _ in range(W)]
             ev[2].record(stream)
-            ab = (workload.view(con, "body_a"), workload.view(con, "body_b"))
+            ab = (workload.view(con, "body_a"), workload.view(con, "body_b"), workload.view(con, "plane"))
             eta, rd = ctx.pdip_measure(st)
             side = hook(step, ctx, con, g, dev_before, sc) if hook else None
             ev[3].record(stream)
@@ -1064,7 +1097,7 @@ def box_leg(args, binding, workload, flush, stream):
             ev4 = torch.cuda.Event(enable_timing=True)
             ev4.record(stream)
             ev4.synchronize()
-            keys = set(zip(ab[0].tolist(), ab[1].tolist()))
+            keys = set(zip(ab[0].tolist(), ab[1].tolist(), ab[2].tolist()))
             rows.append({"step": step, "contacts": con.Nc, "padded_unknowns": con.P,
                          "persisting": None if prev is None else len(keys & prev[3]) / max(1, len(keys)),
                          "ms_assemble": ev[0].elapsed_time(ev[1]), "ms_pdip_window": ev[1].elapsed_time(ev[2]),
@@ -1073,7 +1106,7 @@ def box_leg(args, binding, workload, flush, stream):
                          "solves_converged": sum(int(s_.solve.status == binding.QP_OK and s_.solve.rel_res <= 1e-8)
                                                  for s_ in stats),
                          "krylov_iters": statistics.mean(s_.solve.iters for s_ in stats), "side": side})
-            prev = (ab[0].clone(), ab[1].clone(), g.clone(), keys)
+            prev = (ab[0], ab[1], g.clone(), keys, ab[2])
         return ctx, rows
 
     # training data: window solutions along the trajectories of seeds 2 and 3

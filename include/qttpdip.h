@@ -92,6 +92,8 @@ typedef struct {
   const double* arm_b;      /* [3*Nc] SoA p - x_b                                */
   const unsigned long long* key; /* [Nc] Morton key                              */
   const double* r;          /* [P] padded r = b + D^T M^-1 k (Eq. rdef)          */
+  const int* plane;         /* [Nc] -1 for a sphere pair, 0 the floor, 1 + w side
+                               wall w (which static plane body M stands for)     */
 } qp_contacts;
 
 /* Active set A(q, delta) (Sec. 2.2): every sphere pair with gap
@@ -127,7 +129,9 @@ int pdip_init(qp_ctx_t ctx, qp_state* st, double gn0);
  * its pairs (body_a, body_b, [Nc] each) and its final impulses gamma (padded,
  * prev->slots rows per contact); all device arrays owned by the caller, who
  * must copy them before the ccp_assemble that replaces the contact set.  Each
- * contact of the current set whose pair (a, b) is in prev takes that impulse
+ * contact of the current set whose pair (a, b) -- with prev->plane given, and
+ * the same static plane (qp_contacts.plane), so that a sphere's floor and wall
+ * contacts stay apart -- is in prev takes that impulse
  * moved into its cone's interior: gamma_n = max(gamma_n, gn0), gamma_t scaled
  * to |gamma_t| <= shrink * mu * gamma_n; a new contact takes (gn0, 0, 0);
  * dummy rows 0; lambda_i = -1/f_i (centred at t = 1), t = 1.
@@ -138,6 +142,8 @@ typedef struct {
   const int* body_a;
   const int* body_b;
   const double* gamma;
+  const int* plane;  /* [Nc] the previous qp_contacts.plane, or NULL: match by (a, b)
+                        alone (enough without walls: a sphere has one floor contact) */
 } qp_prev_contacts;
 int pdip_init_warm(qp_ctx_t ctx, qp_state* st, const qp_prev_contacts* prev, double gn0, double shrink);
 
@@ -233,9 +239,33 @@ typedef struct {
   int split;           /* 0: split the scenes whose cost exceeds an even
                           share of the SMs; 1: one block per scene; 2: every
                           scene on two blocks                                */
+  const qtt_t* precond;/* NULL: Jacobi for every scene; else n handles, one
+                          per scene (NULL entries: Jacobi for that scene), a
+                          QTT approximate inverse of the scene's S (or of its
+                          Jacobi-scaled form, as qtt_compress makes it with a
+                          state) with d = that scene's L; the FP32 inner PCG
+                          applies it by one core per pass within the scene's
+                          block(s) (Sec. 3.2 mat-vec); a scene whose QTT PCG
+                          breaks down (a truncated inverse need not be
+                          definite) finishes with Jacobi, stats.fallback = 1 */
+  qp_dtype core_dtype; /* cores of the QTT preconditioners: QP_BF16, else FP32 */
+  int qtt_tile;        /* tile shape of the QTT passes: 0 the measured table of
+                          newton_batch_qtt_tiles; 1 one column item per thread;
+                          2 two items per thread sharing the core staged in
+                          shared memory where r_{k-1} r_k <= 256 and r_k <= 16 */
 } qp_batch_opts;
 int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st, const double* const* rhs,
                          double* const* dx, const qp_batch_opts* opts, qp_solve_stats* stats, int* used);
+
+/* The measured tile shapes of the batched QTT passes for blocks of
+ * block_threads (128, 256, 512 or 1024) threads on this context's device:
+ * tiles_host[c] (c = 0..3 for input ranks <= 4, <= 8, <= 16, above) is 1 (one
+ * column item per thread, inputs in registers) or 2 (two items per thread,
+ * the core staged in shared memory), whichever a one-block probe (a d = 14
+ * QTT of that interior rank, applied four times) timed faster; measured once
+ * per device and block size, then cached.  The automatic tile choice of
+ * newton_solve_batched (qtt_tile = 0) uses this table.                      */
+int newton_batch_qtt_tiles(qp_ctx_t ctx, int block_threads, int* tiles_host /* [4] */);
 
 /* Host only: the cluster jobs newton_solve_batched launches for scenes with
  * the given costs (cost_host[i] >= 0; the solver uses P_i + Nc_i) on num_sms

@@ -50,6 +50,7 @@ class Contacts:
     rb: np.ndarray       # (Nc, 3) arm p - x_b
     key: np.ndarray      # uint64 Morton key
     M: int
+    plane: np.ndarray = None  # int64: -1 for a pair, 0 the floor, 1 + w side wall w
 
     @property
     def Nc(self) -> int:
@@ -201,10 +202,11 @@ def detect(scene, pairs: np.ndarray | None = None) -> Contacts:
     key = morton_keys(p)
     order = np.lexsort((b, a, key))
     a, b, phi, n, p, key = a[order], b[order], phi[order], n[order], p[order], key[order]
+    plane = np.where(a >= M, a - M, -1)  # which static plane, before it is folded into body M
     a = np.minimum(a, M)  # every static plane is body M
     t1, t2 = tangent_frame(n)
     stat = a == M
     xa = np.where(stat[:, None], 0.0, pos[np.minimum(a, M - 1)] if M > 0 else 0.0)
     ra = np.where(stat[:, None], 0.0, p - xa)
     rb = p - pos[b] if b.size else np.zeros((0, 3))
-    return Contacts(a=a, b=b, phi=phi, n=n, t1=t1, t2=t2, p=p, ra=ra, rb=rb, key=key, M=M)
+    return Contacts(a=a, b=b, phi=phi, n=n, t1=t1, t2=t2, p=p, ra=ra, rb=rb, key=key, M=M, plane=plane)

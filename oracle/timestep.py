@@ -44,13 +44,19 @@ def advance(scene, con, gamma: np.ndarray):
     return out
 
 
-def warm_start(prev_a, prev_b, prev_gamma, new_a, new_b, mu, gn0=1.0, shrink=0.9):
-    """(gamma, lambda) for the new contact set from the previous step's impulses."""
-    prev = {(int(a), int(b)): c for c, (a, b) in enumerate(zip(prev_a, prev_b))}
+def warm_start(prev_a, prev_b, prev_gamma, new_a, new_b, mu, gn0=1.0, shrink=0.9, prev_plane=None,
+               new_plane=None):
+    """(gamma, lambda) for the new contact set from the previous step's impulses.
+    A contact persists when its (a, b) pair -- and, with walls, its static
+    plane (-1 for a pair), since a sphere can touch the floor and a wall at
+    once -- occurs in the previous step."""
+    pp = np.full(len(prev_a), -1) if prev_plane is None else prev_plane
+    npl = np.full(len(new_a), -1) if new_plane is None else new_plane
+    prev = {(int(a), int(b), int(w)): c for c, (a, b, w) in enumerate(zip(prev_a, prev_b, pp))}
     Nc = len(new_a)
     gamma = np.zeros(3 * Nc)
     for c in range(Nc):
-        j = prev.get((int(new_a[c]), int(new_b[c])))
+        j = prev.get((int(new_a[c]), int(new_b[c]), int(npl[c])))
         if j is None:
             gamma[3 * c] = gn0
             continue

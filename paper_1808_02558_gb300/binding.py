@@ -24,7 +24,7 @@ QP_CG, QP_BICGSTAB = 0, 1
 QTT_NOALLOC_MAX_VALUES = 1 << 22
 
 SYMBOLS = ["qp_create", "qp_destroy", "qp_status_string", "qp_last_error", "ccp_assemble", "pdip_init",
-           "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "newton_batch_plan", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
+           "newton_apply", "newton_rhs", "newton_solve", "newton_solve_batched", "newton_batch_plan", "newton_batch_qtt_tiles", "pdip_step", "pdip_measure", "pdip_solve", "pdip_init_warm",
            "ccp_advance", "qp_selftest_barrier", "mpnn_forward", "mpnn_grad", "mpnn_adam", "mpnn_warm_start", "qtt_from_host",
            "qtt_free", "qtt_get_dims", "qtt_get_ranks", "qtt_copy_cores_to_host", "qtt_apply", "qtt_set_tensor_cores",
            "qtt_round",
@@ -43,7 +43,7 @@ class Contacts(C.Structure):
     _fields_ = [("M", C.c_int), ("Nc", C.c_int), ("L", C.c_int), ("slots", C.c_int), ("P", C.c_longlong),
                 ("body_a", C.c_void_p), ("body_b", C.c_void_p), ("phi", C.c_void_p), ("frame", C.c_void_p),
                 ("point", C.c_void_p), ("arm_a", C.c_void_p), ("arm_b", C.c_void_p), ("key", C.c_void_p),
-                ("r", C.c_void_p)]
+                ("r", C.c_void_p), ("plane", C.c_void_p)]
 
 
 class State(C.Structure):
@@ -52,12 +52,13 @@ class State(C.Structure):
 
 class BatchOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("block_threads", C.c_int), ("split", C.c_int)]
+                ("block_threads", C.c_int), ("split", C.c_int), ("precond", C.c_void_p), ("core_dtype", C.c_int),
+                ("qtt_tile", C.c_int)]
 
 
 class PrevContacts(C.Structure):
     _fields_ = [("Nc", C.c_int), ("slots", C.c_int), ("body_a", C.c_void_p), ("body_b", C.c_void_p),
-                ("gamma", C.c_void_p)]
+                ("gamma", C.c_void_p), ("plane", C.c_void_p)]
 
 
 class SolveOpts(C.Structure):
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
         "newton_solve_batched": (i, [i, C.POINTER(vp), C.POINTER(C.POINTER(State)), C.POINTER(vp), C.POINTER(vp),
                                      C.POINTER(BatchOpts), C.POINTER(SolveStats), C.POINTER(i)]),
         "newton_batch_plan": (i, [i, C.POINTER(ll), i, i, C.POINTER(i), C.POINTER(i)]),
+        "newton_batch_qtt_tiles": (i, [vp, i, C.POINTER(i)]),
         "ccp_advance": (i, [vp, C.POINTER(Scene), C.POINTER(State), vp, vp, vp]),
         "qp_selftest_barrier": (i, [vp, ll, i, C.POINTER(i)]),
         "mpnn_forward": (i, [vp, vp, C.POINTER(C.c_float), vp]),
@@ -307,10 +309,13 @@ class Context:
         self._check(self.lib.mpnn_warm_start(self.h, C.byref(st), _ptr(out) if out.numel() else None,
                                              float(out_scale), float(gn_min), float(shrink)), "mpnn_warm_start")
 
-    def pdip_init_warm(self, st: State, prev_a, prev_b, prev_gamma, prev_slots=3, gn0=1.0, shrink=0.9):
+    def pdip_init_warm(self, st: State, prev_a, prev_b, prev_gamma, prev_slots=3, gn0=1.0, shrink=0.9,
+                       prev_plane=None):
         """Warm start from the previous step's pairs and impulses (device tensors
-        the caller copied before re-assembly)."""
-        pc = PrevContacts(int(prev_a.numel()), int(prev_slots), _ptr(prev_a), _ptr(prev_b), _ptr(prev_gamma))
+        the caller copied before re-assembly); prev_plane: the previous contacts'
+        plane indices (needed with walls), or None."""
+        pc = PrevContacts(int(prev_a.numel()), int(prev_slots), _ptr(prev_a), _ptr(prev_b), _ptr(prev_gamma),
+                          _ptr(prev_plane) if prev_plane is not None else None)
         self._check(self.lib.pdip_init_warm(self.h, C.byref(st), C.byref(pc), float(gn0), float(shrink)),
                     "pdip_init_warm")
 
@@ -380,6 +385,13 @@ class Context:
     def qtt_apply(self, A: QTT, x, y, core_dtype=QP_F64, vec_dtype=QP_F64):
         self._check(self.lib.qtt_apply(self.h, A.h, _ptr(x), _ptr(y), core_dtype, vec_dtype), "qtt_apply")
 
+    def batch_qtt_tiles(self, block_threads: int) -> list:
+        """Measured tile shapes (1 or 2 column items per thread) of the batched QTT
+        passes for input ranks <= 4, <= 8, <= 16 and above."""
+        t = (C.c_int * 4)()
+        self._check(self.lib.newton_batch_qtt_tiles(self.h, int(block_threads), t), "newton_batch_qtt_tiles")
+        return list(t)
+
     def qtt_set_tensor_cores(self, mode: int):
         """0: CUDA-core steps only; 1: tensor cores for dense cores (default); 2: every core that qualifies."""
         self._check(self.lib.qtt_set_tensor_cores(self.h, int(mode)), "qtt_set_tensor_cores")
@@ -403,11 +415,14 @@ class Context:
 
 
 def newton_solve_batched(ctxs, states, rhs, dx, tol=1e-8, maxit=100000, inner_tol=1e-3, max_outer=60,
-                         block_threads=0, split=0, allow=(QP_NOT_CONVERGED, QP_BREAKDOWN)):
+                         block_threads=0, split=0, allow=(QP_NOT_CONVERGED, QP_BREAKDOWN), precond=None,
+                         core_dtype=QP_F32, qtt_tile=0):
     """Many scenes in one launch (clusters of two thread blocks: a large scene on
     both, small scenes one per block).  ctxs: Contexts on one device; states:
     State or None per scene; rhs, dx: device tensors; split: 0 automatic, 1 one
-    block per scene, 2 every scene on two blocks.
+    block per scene, 2 every scene on two blocks; precond: None (Jacobi) or one
+    QTT (or None) per scene; core_dtype: QP_F32 or QP_BF16 cores; qtt_tile: 0
+    measured tile shapes, 1 one item per thread, 2 two items per thread.
     Returns (per-scene SolveStats list, block size used)."""
     lib = load()
     n = len(ctxs)
@@ -415,7 +430,11 @@ def newton_solve_batched(ctxs, states, rhs, dx, tol=1e-8, maxit=100000, inner_to
     sp = (C.POINTER(State) * n)(*[C.pointer(s) if s is not None else C.POINTER(State)() for s in states])
     rp = (C.c_void_p * n)(*[_ptr(t) for t in rhs])
     dp = (C.c_void_p * n)(*[_ptr(t) for t in dx])
-    opts = BatchOpts(float(tol), int(maxit), float(inner_tol), int(max_outer), int(block_threads), int(split))
+    pre = None
+    if precond is not None:
+        pre = (C.c_void_p * n)(*[(x.h.value if x is not None else None) for x in precond])
+    opts = BatchOpts(float(tol), int(maxit), float(inner_tol), int(max_outer), int(block_threads), int(split),
+                     C.cast(pre, C.c_void_p) if pre is not None else None, int(core_dtype), int(qtt_tile))
     stats = (SolveStats * n)()
     used = C.c_int(0)
     rc = lib.newton_solve_batched(n, ch, sp, rp, dp, C.byref(opts), stats, C.byref(used))

@@ -304,6 +304,7 @@ __global__ void k_gather(int n, int M, const int* __restrict__ perm2, const int*
                          const int* __restrict__ wa, const int* __restrict__ wb, const double* __restrict__ phi_raw,
                          const double* __restrict__ nrm_raw, const double* __restrict__ pt_raw,
                          const double* __restrict__ pos, int* __restrict__ ca, int* __restrict__ cb,
+                         int* __restrict__ cplane,
                          double* __restrict__ phi, double* __restrict__ frame, double* __restrict__ point,
                          double* __restrict__ arm_a, double* __restrict__ arm_b, double* __restrict__ rec64,
                          float* __restrict__ rec32) {
@@ -311,7 +312,8 @@ __global__ void k_gather(int n, int M, const int* __restrict__ perm2, const int*
   if (c >= n) return;
   int j = perm1[perm2[c]];
   int a = wa[j], b = wb[j];
-  if (a > M) a = M;  // every static plane (floor or wall) is body M
+  cplane[c] = a >= M ? a - M : -1;  // which plane, before it is folded into body M
+  if (a > M) a = M;                 // every static plane (floor or wall) is body M
   ca[c] = a;
   cb[c] = b;
   phi[c] = phi_raw[j];
@@ -563,6 +565,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   // final arrays
   c->ca.ensure(n * sizeof(int));
   c->cb.ensure(n * sizeof(int));
+  c->cplane.ensure(n * sizeof(int));
   c->phi.ensure(n * sizeof(double));
   c->frame.ensure(9 * n * sizeof(double));
   c->point.ensure(3 * n * sizeof(double));
@@ -619,7 +622,8 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
     QP_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, k2, k2s, i2, i3, Nc, 0, 3 * MORTON_BITS, st));
     // 5. gather final arrays (contact c <- raw i1[i3[c]])
     k_gather<<<ceil_div(Nc, TB), TB, 0, st>>>(Nc, M, i3, i1, wa, wb, phi_raw, nrm_raw, pt_raw, s->pos,
-                                              c->ca.as<int>(), c->cb.as<int>(), c->phi.as<double>(),
+                                              c->ca.as<int>(), c->cb.as<int>(), c->cplane.as<int>(),
+                                              c->phi.as<double>(),
                                               c->frame.as<double>(), c->point.as<double>(), c->arm_a.as<double>(),
                                               c->arm_b.as<double>(), c->rec64.as<double>(),
                                               c->rec32.as<float>());
@@ -665,6 +669,7 @@ static void assemble(qp_ctx* c, const qp_scene* s, qp_contacts* out) {
   out->arm_b = c->arm_b.as<double>();
   out->key = c->key.as<unsigned long long>();
   out->r = c->r.as<double>();
+  out->plane = c->cplane.as<int>();
 }
 
 }  // namespace qp

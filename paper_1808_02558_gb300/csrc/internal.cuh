@@ -82,7 +82,7 @@ struct qp_ctx {
   bool have_contacts = false;
 
   // contact arrays (FP64 master + FP32 copies for the mixed-precision path)
-  qp::Buf ca, cb, phi, frame, point, arm_a, arm_b, key, r;
+  qp::Buf ca, cb, phi, frame, point, arm_a, arm_b, key, r, cplane;
   qp::Buf rec64, rec32;  // [Nc][16] contact records: n t1 t2 ra rb pad
   // body arrays
   qp::Buf inv_m, inv_I, inv_m32, inv_I32, bptr, inc;
@@ -108,6 +108,7 @@ struct qp_ctx {
   qp::Buf fused_pool;
   qp::Buf mp_act, mp_w, mp_grad, mp_sum;  // learned warm start: activations, BF16 weights, scratch
   qp::Buf batch64, batch32, batch_table;  // batched solves: per-scene vectors; table (first context)
+  qp::Buf batch_qw, tune_buf;  // batched QTT work buffers; tile-shape probe data
   qp::Buf tc_err;  // error flag of the tensor-core QTT step
   int qtt_tc_mode = 1;  // tensor-core QTT steps: 0 never, 1 dense cores, 2 every core that fits
 };

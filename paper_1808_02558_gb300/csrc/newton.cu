@@ -1457,10 +1457,14 @@ struct BatchScene {
   float* v32;            // 7 [P] FP32 vectors: b, e, r, z, p, p', q
   long long P;
   int nrow;
+  const QttDev* qtt;     // the scene's QTT preconditioner (device copy), or null: Jacobi
+  float* qw;             // QTT work: two [P * rmax] FP32 buffers
+  int qtt_scaled;        // X approximates the inverse of D^-1/2 S D^-1/2
+  int qtt_bf16;          // cores in BF16 (else FP32)
 };
 
 struct BatchOut {
-  int iters, outer, status, pad;
+  int iters, outer, status, fallback;  // fallback: the QTT preconditioner broke down, Jacobi finished
   double rel;
 };
 
@@ -1599,12 +1603,138 @@ __device__ int block_inner_pcg(const BatchScene& S, float tol, int maxit, int& i
   return 1;
 }
 
+// z = X r through a QTT preconditioner by the threads of one group (one core
+// per pass, group-synchronised), z = D^-1/2 X D^-1/2 r when X approximates the
+// inverse of the Jacobi-scaled matrix (Sec. 3.2 mat-vec, as qtt_precond does it
+// for the whole grid).  Tile shape per core, by the class of its input rank
+// r_k (<= 4, <= 8, <= 16): bit c of tilemask set = two column items per thread
+// sharing the core staged in shared memory (r_{k-1} r_k <= 256); clear, or a
+// rank above 16 = one item per thread, its inputs in registers.  Rows of r
+// from nrow on must be zero.
+template <int NTB, class TC>
+__device__ void group_qtt_apply(const QttDev& q, int scaled, const float* dinv, int nrow, long long P, float* qw,
+                                const float* r, float* z, Grp& g, unsigned tilemask) {
+  __shared__ float gc[4 * 16 * 16];
+  const int t = g.T, NT = g.NT;
+  const long long items = P >> 1;
+  float* w0 = qw;
+  float* w1 = qw + (size_t)P * q.rmax;
+  const float* in = r;
+  if (scaled) {
+    for (long long i = t; i < P; i += NT) w1[i] = i < nrow ? sqrtf(dinv[i]) * r[i] : 0.f;
+    grp_sync(g);
+    in = w1;  // read by the first pass only, which writes w0
+  }
+  int pass = 0;
+  for (int k = q.d; k >= 1; --k, ++pass) {
+    float* out = k == 1 ? z : ((pass & 1) ? w1 : w0);
+    const int r0 = q.ranks[k - 1], r1 = q.ranks[k];
+    const int cls = r1 <= 4 ? 0 : (r1 <= 8 ? 1 : (r1 <= 16 ? 2 : 3));
+    if (cls < 3 && ((tilemask >> cls) & 1u) && r0 * r1 <= 256) {
+      if (cls == 0) qtt_step_block<4, float, float, TC>(q, k, in, out, items, gc, t, NT);
+      else if (cls == 1) qtt_step_block<8, float, float, TC>(q, k, in, out, items, gc, t, NT);
+      else qtt_step_block<16, float, float, TC>(q, k, in, out, items, gc, t, NT);
+    } else {
+      for (long long it = t; it < items; it += NT) qtt_step_any<float, float, TC>(q, k, in, out, it);
+    }
+    grp_sync(g);
+    in = out;
+  }
+  if (scaled) {
+    for (long long i = t; i < nrow; i += NT) z[i] *= sqrtf(dinv[i]);
+    grp_sync(g);
+  }
+}
+
+// The FP32 inner PCG of block_inner_pcg with the scene's QTT preconditioner:
+// after each update of r the whole group applies z = M^-1 r, then r.z is summed.
+template <int NTB, class TC>
+__device__ int block_inner_pcg_qtt(const BatchScene& S, float tol, int maxit, int& iters, Grp& g, unsigned tilemask) {
+  const SysView<float>& s = S.s32;
+  const int nrow = S.nrow, t = g.T, NT = g.NT;
+  const long long P = S.P;
+  float* b = S.v32;
+  float* e = b + P;
+  float* r = e + P;
+  float* z = r + P;
+  float* pa = z + P;
+  float* pb = pa + P;
+  float* q = pb + P;
+  float a0[1] = {0.f};
+  for (long long i = t; i < P; i += NT) {
+    const float bi = i < nrow ? b[i] : 0.f;
+    e[i] = 0.f;
+    r[i] = bi;
+    a0[0] += bi * bi;
+  }
+  group_sum<NTB>(a0, g);
+  const float bb = a0[0];
+  if (bb == 0.f) return 0;
+  const float stop = tol * tol * bb;
+  group_qtt_apply<NTB, TC>(*S.qtt, S.qtt_scaled, S.dinv32, nrow, P, S.qw, r, z, g, tilemask);
+  float a1[1] = {0.f};
+  for (int i = t; i < nrow; i += NT) a1[0] += r[i] * z[i];
+  group_sum<NTB>(a1, g);
+  float rz = a1[0];
+  float* pold = pa;
+  float* pnew = pb;
+  float beta = 0.f;
+  for (int it = 0; it < maxit; ++it) {
+    if (!(rz > 0.f)) return 2;
+    const Operand<float> dir{z, it == 0 ? nullptr : pold, beta};
+    for (int bd = t; bd < s.M; bd += NT) body_gather(s, dir, bd);
+    grp_sync(g);
+    float a2[1] = {0.f};
+    for (int c = t; c < s.Nc; c += NT) a2[0] += contact_apply(s, dir, q, c, pnew);
+    group_sum<NTB>(a2, g);
+    const float pq = a2[0];
+    if (!(pq > 0.f)) return 2;
+    const float alpha = rz / pq;
+    float a3[1] = {0.f};
+    for (int i = t; i < nrow; i += NT) {
+      e[i] += alpha * pnew[i];
+      const float ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      a3[0] += ri * ri;
+    }
+    group_sum<NTB>(a3, g);
+    ++iters;
+    if (a3[0] <= stop) return 0;
+    group_qtt_apply<NTB, TC>(*S.qtt, S.qtt_scaled, S.dinv32, nrow, P, S.qw, r, z, g, tilemask);
+    float a4[1] = {0.f};
+    for (int i = t; i < nrow; i += NT) a4[0] += r[i] * z[i];
+    group_sum<NTB>(a4, g);
+    beta = a4[0] / rz;
+    rz = a4[0];
+    float* tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+  }
+  return 1;
+}
+
+// Tile-shape probe of the autotuner: one block applies a QTT `reps` times with
+// the given tile mask (the batched kernel runs one scene per block).
+template <int NTB>
+__global__ void __launch_bounds__(NTB) k_qtt_tile_probe(QttDev q, const float* x, float* y, float* qw, unsigned tilemask,
+                                                        int reps) {
+  Grp g;
+  g.T = threadIdx.x;
+  g.NT = NTB;
+  g.split = false;
+  g.ph = 0;
+  const long long P = 1LL << q.d;
+  for (int i = 0; i < reps; ++i) group_qtt_apply<NTB, float>(q, 0, nullptr, (int)P, P, qw, x, y, g, tilemask);
+}
+
 // One job per cluster: jobs[j] = (scene, -2) runs that scene on both blocks;
 // (a, b) runs scene a on block rank 0 and scene b (b >= 0) on rank 1.
-template <int NTB>
+// QTT = true adds the per-scene QTT preconditioner (scenes with S.qtt set; the
+// others keep Jacobi); QTT = false is the Jacobi-only kernel.
+template <int NTB, bool QTT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTB)
     k_pcg_batched(const BatchScene* __restrict__ tab, const int2* __restrict__ jobs, double tol, double inner_tol,
-                  int maxit, int max_outer, BatchOut* __restrict__ out) {
+                  int maxit, int max_outer, BatchOut* __restrict__ out, unsigned tilemask) {
   const int rank = (int)cg::this_cluster().block_rank();
   const int2 job = jobs[blockIdx.x >> 1];
   Grp g;
@@ -1643,7 +1773,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTB)
   for (int i = t; i < S.nrow; i += NT) bn[0] += S.rhs[i] * S.rhs[i];
   group_sum<NTB>(bn, g);
   const double bnorm = sqrt(bn[0]);
-  int iters = 0, outer = 0, status = 0;
+  int iters = 0, outer = 0, status = 0, fell_back = 0;
   double rel = 0.0;
   if (bnorm > 0.0) {
     for (outer = 0;; ++outer) {
@@ -1676,7 +1806,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTB)
       for (int i = t; i < S.nrow; i += NT) S.v32[i] = (float)(S.r64[i] * inv);
       grp_sync(g);
       const int before = iters;
-      const int st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters, g);
+      int st;
+      if constexpr (QTT) {
+        if (S.qtt && !fell_back) {
+          st = S.qtt_bf16 ? block_inner_pcg_qtt<NTB, __nv_bfloat16>(S, (float)inner_tol, maxit - iters, iters, g, tilemask)
+                          : block_inner_pcg_qtt<NTB, float>(S, (float)inner_tol, maxit - iters, iters, g, tilemask);
+          // a truncated QTT inverse need not be definite: on a breakdown the
+          // scene continues with the Jacobi preconditioner (as newton_solve does)
+          if (st == 2) {
+            fell_back = 1;
+            st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters, g);
+          }
+        } else {
+          st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters, g);
+        }
+      } else {
+        st = block_inner_pcg<NTB>(S, (float)inner_tol, maxit - iters, iters, g);
+      }
       const float* e = S.v32 + S.P;
       for (int i = t; i < S.nrow; i += NT) S.dx[i] += rn * (double)e[i];
       grp_sync(g);
@@ -1690,6 +1836,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTB)
     out[sid].iters = iters;
     out[sid].outer = outer;
     out[sid].status = status;
+    out[sid].fallback = fell_back;
     out[sid].rel = rel;
   }
   // a block's shared memory must outlive the other block's last read of it
@@ -2951,18 +3098,92 @@ static qp_solve_stats solve(qp_ctx* c, const double* rhs, double* dx, const qp_s
 // Batched solve: build the scene table, group the scenes into cluster jobs
 // (large scenes split over two blocks, small ones paired), launch one cluster
 // per job (block size given or measured), read the per-scene results.
+template <bool QTT>
+static void launch_batched_t(qp_ctx* c0, int nt, int grid, const BatchScene* tab, const int2* jobs, double tol,
+                             double itol, int maxit, int mo, BatchOut* out, unsigned tm) {
+  switch (nt) {
+    case 128: k_pcg_batched<128, QTT><<<grid, 128, 0, c0->stream>>>(tab, jobs, tol, itol, maxit, mo, out, tm); break;
+    case 256: k_pcg_batched<256, QTT><<<grid, 256, 0, c0->stream>>>(tab, jobs, tol, itol, maxit, mo, out, tm); break;
+    case 512: k_pcg_batched<512, QTT><<<grid, 512, 0, c0->stream>>>(tab, jobs, tol, itol, maxit, mo, out, tm); break;
+    default: k_pcg_batched<1024, QTT><<<grid, 1024, 0, c0->stream>>>(tab, jobs, tol, itol, maxit, mo, out, tm); break;
+  }
+}
+
 static void launch_batched(qp_ctx* c0, int nt, int njobs, const BatchScene* tab, const int2* jobs,
-                           const qp_batch_opts* o, BatchOut* out) {
+                           const qp_batch_opts* o, BatchOut* out, bool qtt, unsigned tilemask) {
   const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-3;
   const int mo = o->max_outer > 0 ? o->max_outer : 50;
   const int grid = 2 * njobs;
-  switch (nt) {
-    case 128: k_pcg_batched<128><<<grid, 128, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
-    case 256: k_pcg_batched<256><<<grid, 256, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
-    case 512: k_pcg_batched<512><<<grid, 512, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
-    default: k_pcg_batched<1024><<<grid, 1024, 0, c0->stream>>>(tab, jobs, o->tol, itol, o->maxit, mo, out); break;
-  }
+  if (qtt) launch_batched_t<true>(c0, nt, grid, tab, jobs, o->tol, itol, o->maxit, mo, out, tilemask);
+  else launch_batched_t<false>(c0, nt, grid, tab, jobs, o->tol, itol, o->maxit, mo, out, tilemask);
   QP_CUDA(cudaGetLastError());
+}
+
+// Measured tile shapes of the batched QTT apply, per (device, block size): for
+// each input-rank class (<= 4, <= 8, <= 16) one block applies a d = 14 QTT of
+// that interior rank with one and with two column items per thread (4 applies
+// each, timed with events after a warm-up), and the faster shape sets the bit.
+static std::mutex g_tile_mu;
+static std::map<std::pair<int, int>, unsigned> g_tiles;
+
+template <int NTB>
+static float time_tile_probe(qp_ctx* c, const QttDev& q, const float* x, float* y, float* qw, unsigned tm) {
+  k_qtt_tile_probe<NTB><<<1, NTB, 0, c->stream>>>(q, x, y, qw, tm, 1);
+  QP_CUDA(cudaEventRecord(c->ev0, c->stream));
+  k_qtt_tile_probe<NTB><<<1, NTB, 0, c->stream>>>(q, x, y, qw, tm, 4);
+  QP_CUDA(cudaEventRecord(c->ev1, c->stream));
+  QP_CUDA(cudaEventSynchronize(c->ev1));
+  QP_CUDA(cudaGetLastError());
+  float ms = 0.f;
+  QP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  return ms;
+}
+
+static unsigned batch_tile_mask(qp_ctx* c, int nt) {
+  const auto key = std::make_pair(c->device, nt);
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) return it->second;
+  }
+  constexpr int d = 14;
+  const long long P = 1LL << d;
+  unsigned mask = 0;
+  for (int cls = 0; cls < 3; ++cls) {
+    const int R = 4 << cls;
+    QttDev q;
+    q.d = d;
+    q.rmax = R;
+    long long off = 0;
+    for (int k = 0; k <= d; ++k) {
+      q.ranks[k] = (k == 0 || k == d) ? 1 : R;
+      q.off[k] = off;
+      if (k < d) off += (long long)((k == 0) ? 1 : R) * 4 * ((k + 1 == d) ? 1 : R);
+    }
+    // deterministic core values of unit scale (any finite values time the same)
+    std::vector<float> hc((size_t)off);
+    for (size_t i = 0; i < hc.size(); ++i) hc[i] = (float)(((i * 2654435761u) % 1000u) / 1000.0 - 0.5);
+    char* buf = static_cast<char*>(c->tune_buf.ensure(sizeof(float) * ((size_t)off + 2 * (size_t)P + 2 * (size_t)P * R)));
+    float* cores = reinterpret_cast<float*>(buf);
+    float* x = cores + off;
+    float* y = x + P;
+    float* qw = y + P;
+    QP_CUDA(cudaMemcpyAsync(cores, hc.data(), sizeof(float) * (size_t)off, cudaMemcpyHostToDevice, c->stream));
+    QP_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)P, c->stream));
+    q.cores = cores;
+    float t1 = 0.f, t2 = 0.f;
+    const unsigned bit = 1u << cls;
+    switch (nt) {
+      case 128: t1 = time_tile_probe<128>(c, q, x, y, qw, 0u); t2 = time_tile_probe<128>(c, q, x, y, qw, bit); break;
+      case 256: t1 = time_tile_probe<256>(c, q, x, y, qw, 0u); t2 = time_tile_probe<256>(c, q, x, y, qw, bit); break;
+      case 512: t1 = time_tile_probe<512>(c, q, x, y, qw, 0u); t2 = time_tile_probe<512>(c, q, x, y, qw, bit); break;
+      default: t1 = time_tile_probe<1024>(c, q, x, y, qw, 0u); t2 = time_tile_probe<1024>(c, q, x, y, qw, bit); break;
+    }
+    if (t2 < t1) mask |= bit;
+  }
+  std::lock_guard<std::mutex> lock(g_tile_mu);
+  g_tiles[key] = mask;
+  return mask;
 }
 
 // Cluster jobs from per-scene costs: with split = 0 a scene whose cost exceeds
@@ -3040,14 +3261,46 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
     work += c->P;
   }
   QP_REQUIRE(o->split >= 0 && o->split <= 2, QP_INVALID_ARG, "newton_solve_batched: split must be 0, 1 or 2");
+  QP_REQUIRE(o->qtt_tile >= 0 && o->qtt_tile <= 2, QP_INVALID_ARG, "newton_solve_batched: qtt_tile must be 0, 1 or 2");
+  // per-scene QTT preconditioners (FP32 or BF16 copies of the cores)
+  const qp_dtype cdt = o->core_dtype == QP_BF16 ? QP_BF16 : QP_F32;
+  std::vector<QttDev> qdev;
+  std::vector<int> qidx(n, -1);
+  for (int i = 0; o->precond && i < n; ++i) {
+    qp_qtt* X = o->precond[i];
+    if (!X) continue;
+    qp_ctx* c = ctxs[i];
+    QP_REQUIRE(X->d == c->L && X->d <= 64, QP_INVALID_ARG, "newton_solve_batched: preconditioner size does not match 2^L");
+    qtt_prepare_copies(c, X, cdt);
+    QttDev q;
+    q.d = X->d;
+    q.rmax = 1;
+    for (int k = 0; k <= X->d; ++k) {
+      q.ranks[k] = X->ranks[k];
+      q.off[k] = X->offset[k];
+      if (X->ranks[k] > q.rmax) q.rmax = X->ranks[k];
+    }
+    q.cores = cdt == QP_BF16 ? (const void*)X->cores16 : (const void*)X->cores32;
+    BatchScene& b = tab[i];
+    b.qw = static_cast<float*>(c->batch_qw.ensure(2 * (size_t)c->P * q.rmax * sizeof(float)));
+    b.qtt_scaled = X->scaled;
+    b.qtt_bf16 = cdt == QP_BF16 ? 1 : 0;
+    qidx[i] = (int)qdev.size();
+    qdev.push_back(q);
+  }
+  const bool use_qtt = !qdev.empty();
   const std::vector<int2> jobs = batch_jobs(cost, c0->num_sms, o->split);
   const int nj = (int)jobs.size();
-  // table, jobs and outputs in one device buffer of ctxs[0]
+  // table, jobs, outputs and QTT views in one device buffer of ctxs[0]
+  auto up = [](size_t b) { return ((b + 255) / 256) * 256; };
   const size_t tb = sizeof(BatchScene) * n, ob = sizeof(int2) * n, rb = sizeof(BatchOut) * n;
-  char* buf = static_cast<char*>(c0->batch_table.ensure(tb + 256 + ob + 256 + rb));
+  const size_t qb = sizeof(QttDev) * qdev.size();
+  char* buf = static_cast<char*>(c0->batch_table.ensure(up(tb) + up(ob) + up(rb) + qb + 256));
   BatchScene* dtab = reinterpret_cast<BatchScene*>(buf);
-  int2* djobs = reinterpret_cast<int2*>(buf + ((tb + 255) / 256) * 256);
-  BatchOut* dout = reinterpret_cast<BatchOut*>(buf + ((tb + 255) / 256) * 256 + ((ob + 255) / 256) * 256);
+  int2* djobs = reinterpret_cast<int2*>(buf + up(tb));
+  BatchOut* dout = reinterpret_cast<BatchOut*>(buf + up(tb) + up(ob));
+  QttDev* dq = reinterpret_cast<QttDev*>(buf + up(tb) + up(ob) + up(rb));
+  for (int i = 0; i < n; ++i) tab[i].qtt = qidx[i] >= 0 ? dq + qidx[i] : nullptr;
   // the other contexts' pending work (assembly, states) comes first
   for (int i = 0; i < n; ++i)
     if (ctxs[i] != c0) {
@@ -3056,13 +3309,21 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
     }
   QP_CUDA(cudaMemcpyAsync(dtab, tab.data(), tb, cudaMemcpyHostToDevice, c0->stream));
   QP_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(int2) * nj, cudaMemcpyHostToDevice, c0->stream));
+  if (use_qtt) QP_CUDA(cudaMemcpyAsync(dq, qdev.data(), qb, cudaMemcpyHostToDevice, c0->stream));
+  auto tiles_for = [&](int threads) -> unsigned {
+    if (!use_qtt) return 0u;
+    if (o->qtt_tile == 1) return 0u;
+    if (o->qtt_tile == 2) return 7u;
+    return batch_tile_mask(c0, threads);
+  };
   int nt = o->block_threads;
   QP_REQUIRE(nt == 0 || nt == 128 || nt == 256 || nt == 512 || nt == 1024, QP_INVALID_ARG,
              "newton_solve_batched: block_threads must be 0, 128, 256, 512 or 1024");
   if (nt == 0) {
     long long cls = 1;
     while (cls < work / n) cls <<= 1;
-    const auto key = std::make_pair(c0->device, (cls * 4096 + (n < 4096 ? n / 64 : 64)) * 4 + o->split);
+    const auto key = std::make_pair(c0->device, ((cls * 4096 + (n < 4096 ? n / 64 : 64)) * 4 + o->split) * 2 +
+                                                    (use_qtt ? 1 : 0));
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune.find(key);
@@ -3071,8 +3332,9 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
     if (nt == 0) {
       float best = 1e30f;
       for (int cand : {256, 512, 1024}) {
+        const unsigned tm = tiles_for(cand);
         QP_CUDA(cudaEventRecord(c0->ev0, c0->stream));
-        launch_batched(c0, cand, nj, dtab, djobs, o, dout);
+        launch_batched(c0, cand, nj, dtab, djobs, o, dout, use_qtt, tm);
         QP_CUDA(cudaEventRecord(c0->ev1, c0->stream));
         QP_CUDA(cudaEventSynchronize(c0->ev1));
         float ms = 0;
@@ -3086,8 +3348,9 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
       g_tune[key] = nt;
     }
   }
+  const unsigned tm = tiles_for(nt);
   QP_CUDA(cudaEventRecord(c0->ev0, c0->stream));
-  launch_batched(c0, nt, nj, dtab, djobs, o, dout);
+  launch_batched(c0, nt, nj, dtab, djobs, o, dout, use_qtt, tm);
   QP_CUDA(cudaEventRecord(c0->ev1, c0->stream));
   std::vector<BatchOut> res(n);
   QP_CUDA(cudaMemcpyAsync(res.data(), dout, rb, cudaMemcpyDeviceToHost, c0->stream));
@@ -3106,7 +3369,7 @@ static int batched_solve(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
       stats[i].outer = res[i].outer;
       stats[i].rel_res = res[i].rel;
       stats[i].ms = ms;
-      stats[i].fallback = 0;
+      stats[i].fallback = res[i].fallback;
     }
     if (rc == QP_OK && code != QP_OK) rc = code;
   }
@@ -3232,6 +3495,18 @@ int newton_solve_batched(int n, const qp_ctx_t* ctxs, const qp_state* const* st,
   API_BEGIN(c)
   QP_REQUIRE(o->tol > 0 && o->maxit > 0, QP_INVALID_ARG, "newton_solve_batched: tol > 0 and maxit > 0 required");
   return batched_solve(n, ctxs, st, rhs, dx, o, stats, used);
+  API_END(c)
+}
+
+int newton_batch_qtt_tiles(qp_ctx_t c, int block_threads, int* tiles) {
+  if (!c || !tiles) return QP_INVALID_ARG;
+  API_BEGIN(c)
+  QP_REQUIRE(block_threads == 128 || block_threads == 256 || block_threads == 512 || block_threads == 1024,
+             QP_INVALID_ARG, "newton_batch_qtt_tiles: block_threads must be 128, 256, 512 or 1024");
+  QP_CUDA(cudaSetDevice(c->device));
+  const unsigned m = batch_tile_mask(c, block_threads);
+  for (int k = 0; k < 3; ++k) tiles[k] = ((m >> k) & 1u) ? 2 : 1;
+  tiles[3] = 1;
   API_END(c)
 }
 

@@ -7,14 +7,22 @@
 namespace qp {
 namespace {
 
-__device__ __forceinline__ unsigned long long pair_key(int a, int b) {
+// Key of a contact: (a, b), with a static plane's body M replaced by M + its
+// plane index (floor 0, wall w: 1 + w), so a sphere's floor and wall contacts
+// differ; without plane indices (plane == nullptr) the pair alone.
+__device__ __forceinline__ unsigned long long pair_key(int a, int b, const int* plane, int i, int M) {
+  if (plane) {
+    const int w = __ldg(plane + i);
+    if (w >= 0) a = M + w;
+  }
   return ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
 }
 
-__global__ void k_prev_keys(int n, const int* __restrict__ a, const int* __restrict__ b,
-                            unsigned long long* __restrict__ key, int* __restrict__ idx) {
+__global__ void k_prev_keys(int n, int M, const int* __restrict__ a, const int* __restrict__ b,
+                            const int* __restrict__ plane, unsigned long long* __restrict__ key,
+                            int* __restrict__ idx) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    key[i] = pair_key(__ldg(a + i), __ldg(b + i));
+    key[i] = pair_key(__ldg(a + i), __ldg(b + i), plane, i, M);
     idx[i] = i;
   }
 }
@@ -23,8 +31,8 @@ __global__ void k_prev_keys(int n, const int* __restrict__ a, const int* __restr
 // two multipliers.  A contact whose pair was in the previous set takes that
 // impulse moved into its cone's interior (gamma_n >= gn0, |gamma_t| <=
 // shrink mu gamma_n); a new contact takes (gn0, 0, 0); lambda = -1/f.
-__global__ void k_pdip_warm(int Nc, int slots, long long P, double mu, double gn0, double shrink,
-                            const int* __restrict__ ca, const int* __restrict__ cb,
+__global__ void k_pdip_warm(int Nc, int M, int slots, long long P, double mu, double gn0, double shrink,
+                            const int* __restrict__ ca, const int* __restrict__ cb, const int* __restrict__ cplane,
                             const unsigned long long* __restrict__ skey, const int* __restrict__ sidx, int nprev,
                             int pslots, const double* __restrict__ pgamma, double* __restrict__ gamma,
                             double* __restrict__ lambda) {
@@ -36,7 +44,7 @@ __global__ void k_pdip_warm(int Nc, int slots, long long P, double mu, double gn
       gamma[i] = 0.0;
       continue;
     }
-    const unsigned long long k = pair_key(__ldg(ca + c), __ldg(cb + c));
+    const unsigned long long k = pair_key(__ldg(ca + c), __ldg(cb + c), cplane, (int)c, M);
     int lo = 0, hi = nprev;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -89,7 +97,8 @@ extern "C" int pdip_init_warm(qp_ctx_t c, qp_state* st, const qp_prev_contacts* 
     int* idx = reinterpret_cast<int*>(key + 2 * nn);
     int* sidx = idx + nn;
     if (n > 0) {
-      k_prev_keys<<<(n + 255) / 256, 256, 0, c->stream>>>(n, prev->body_a, prev->body_b, key, idx);
+      k_prev_keys<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->M, prev->body_a, prev->body_b, prev->plane, key,
+                                                          idx);
       QP_CUDA(cudaGetLastError());
       size_t tmp_bytes = 0;
       QP_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key, skey, idx, sidx, n, 0, 64, c->stream));
@@ -98,9 +107,10 @@ extern "C" int pdip_init_warm(qp_ctx_t c, qp_state* st, const qp_prev_contacts* 
     }
     int grid = (int)((c->P + 255) / 256);
     if (grid > c->num_sms * 8) grid = c->num_sms * 8;
-    k_pdip_warm<<<grid, 256, 0, c->stream>>>(c->Nc, c->slots, c->P, c->mu, gn0, shrink, c->ca.as<int>(),
-                                             c->cb.as<int>(), skey, sidx, n, prev->slots, prev->gamma, st->gamma,
-                                             st->lambda);
+    // plane indices take part in the keys on both sides, or on neither
+    k_pdip_warm<<<grid, 256, 0, c->stream>>>(c->Nc, c->M, c->slots, c->P, c->mu, gn0, shrink, c->ca.as<int>(),
+                                             c->cb.as<int>(), prev->plane ? c->cplane.as<int>() : nullptr, skey, sidx,
+                                             n, prev->slots, prev->gamma, st->gamma, st->lambda);
     QP_CUDA(cudaGetLastError());
     st->t = 1.0;
   } catch (const Error& e) {

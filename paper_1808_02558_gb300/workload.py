@@ -45,8 +45,9 @@ def view(con, name: str, device="cuda") -> torch.Tensor:
     """Copy a context-owned contact array (raw device pointer) into a new tensor."""
     Nc = con.Nc
     count = {"body_a": Nc, "body_b": Nc, "phi": Nc, "frame": 9 * Nc, "point": 3 * Nc, "arm_a": 3 * Nc,
-             "arm_b": 3 * Nc, "key": Nc, "r": con.P}[name]
-    dt = {"body_a": torch.int32, "body_b": torch.int32, "key": torch.int64}.get(name, torch.float64)
+             "arm_b": 3 * Nc, "key": Nc, "r": con.P, "plane": Nc}[name]
+    dt = {"body_a": torch.int32, "body_b": torch.int32, "key": torch.int64, "plane": torch.int32}.get(name,
+                                                                                                    torch.float64)
     if count == 0:
         return torch.empty(0, dtype=dt, device=device)
     arr = _DeviceArray(getattr(con, name), count, _TYPESTR[dt])

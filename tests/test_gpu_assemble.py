@@ -25,6 +25,7 @@ def check_bitexact(pb: Problem):
     a = to_np(workload.view(con, "body_a"))
     b = to_np(workload.view(con, "body_b"))
     assert np.array_equal(a, o.a) and np.array_equal(b, o.b)
+    assert np.array_equal(to_np(workload.view(con, "plane")), o.plane)
     key = to_np(workload.view(con, "key")).view(np.uint64)
     assert np.array_equal(key, o.key)
     assert np.array_equal(to_np(workload.view(con, "phi")), o.phi)

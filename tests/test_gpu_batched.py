@@ -123,3 +123,69 @@ def test_split_and_unsplit_solves_agree(ctx):
     for x in out.values():
         assert np.linalg.norm(b - S @ x) <= 1.05e-10 * np.linalg.norm(b)
     assert_close(out[2], out[1], 1e-6, floor_rel=1e-2, what="split vs unsplit solve")
+
+
+@pytest.mark.parametrize("tile,cdt", [(0, binding.QP_F32), (1, binding.QP_F32), (2, binding.QP_BF16)])
+def test_batched_qtt_preconditioner(ctx, tile, cdt):
+    """Scenes with their own QTT inverse of their Jacobi-scaled Schur matrix
+    (compressed with the state) next to scenes on Jacobi, in one launch.  The
+    scenes of up to 2^6 unknowns get exact inverses (ranks up to 64: every rank
+    class of the tile table occurs) and take the iteration count of the
+    single-scene QTT-PCG with the same inverse; a 2^9 scene gets a truncated one
+    (rank 10), which may break down and then finish with Jacobi, as the
+    single-scene solver does.  All: residual 1e-10 against the oracle S."""
+    sc = [lattice_scene(2, 12, mu=0.4), sphere_on_plane((0.3, 0.1, -0.2)), lattice_scene(2, 21, mu=0.7),
+          lattice_scene(4, 14, mu=0.6), lattice_scene(3, 40, mu=0.8)]
+    rank = [64, 64, 64, 10, None]
+    pbs, states, rhs, dx, keep, X = [], [], [], [], [], []
+    for i, (s, rk) in enumerate(zip(sc, rank)):
+        pb = Problem(ctx, s)
+        g, lam = interior_point(pb, i)
+        gd, ld, st = pb.state(g, lam)
+        r = torch.empty(pb.P, dtype=torch.float64, device="cuda")
+        pb.ctx.newton_rhs(st, r)
+        pbs.append((pb, g, lam))
+        states.append(st)
+        rhs.append(r)
+        dx.append(torch.full_like(r, 9.0))
+        keep.append((gd, ld))
+        if rk is None:
+            X.append(None)
+            continue
+        eps = 1e-7 if rk == 64 else 1e-2
+        S_tt = pb.ctx.qtt_compress(st, eps, rk)
+        X.append(pb.ctx.qtt_inverse(S_tt, eps, rk, sweeps=4))
+        S_tt.free()
+    assert X[0].d == 6 and X[1].d == 2
+    stats, used = binding.newton_solve_batched([p[0].ctx for p in pbs], states, rhs, dx, tol=1e-10, maxit=20000,
+                                               block_threads=256, allow=(), precond=X, core_dtype=cdt,
+                                               qtt_tile=tile)
+    for (pb, g, lam), st, r, x, s, Xi, rk in zip(pbs, states, rhs, dx, stats, X, rank):
+        assert s.status == binding.QP_OK
+        S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
+        b = pb.unpad(to_np(r))
+        xs = pb.unpad(to_np(x))
+        assert np.linalg.norm(b - S @ xs) <= 1.05e-10 * np.linalg.norm(b)
+        if rk != 64:
+            continue
+        assert s.fallback == 0
+        one = torch.empty_like(r)
+        so = pb.ctx.solve_opts(binding.QP_QTT_PCG, Xi, tol=1e-10, maxit=20000, mixed=1, inner_tol=1e-3,
+                               max_outer=60, core_dtype=cdt)
+        s1 = pb.ctx.newton_solve(st, r, one, so, allow=())
+        assert s1.fallback == 0
+        assert abs(s.iters - s1.iters) <= max(3, 0.2 * s1.iters), (s.iters, s1.iters)
+        assert_close(xs, pb.unpad(to_np(one)), 1e-6, floor_rel=1e-2, what="batched vs single QTT solve")
+    for Xi in X:
+        if Xi is not None:
+            Xi.free()
+
+
+def test_batched_qtt_tile_table(ctx):
+    for nt in (256, 1024):
+        t = ctx.batch_qtt_tiles(nt)
+        assert len(t) == 4 and all(v in (1, 2) for v in t[:3]) and t[3] == 1
+        assert ctx.batch_qtt_tiles(nt) == t  # measured once, then cached
+    with pytest.raises(binding.QPError) as e:
+        ctx.batch_qtt_tiles(300)
+    assert e.value.code == binding.QP_INVALID_ARG

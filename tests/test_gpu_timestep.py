@@ -7,7 +7,7 @@ import torch
 from gpu_common import Problem, assert_close, dev, to_np
 from oracle import contacts as oc, pdip, qp, timestep
 from paper_1808_02558_gb300 import binding, workload
-from synth import random_vector, scene_for
+from synth import box_scene, random_vector, scene_for
 from test_gpu_newton import interior_point
 from test_oracle_pdip import closed_form
 from test_oracle_qp import sphere_on_plane
@@ -84,9 +84,11 @@ def test_warm_start_after_step_matches_oracle(ctx, slots):
     assert persist >= 0.9 * oc1.Nc
 
 
-def test_three_time_steps_match_oracle(ctx):
-    """assemble -> (warm) init -> 4 PDIP iterations -> advance, three times."""
-    s = scene_for("pile8", 5)
+@pytest.mark.parametrize("walled", [False, True])
+def test_three_time_steps_match_oracle(ctx, walled):
+    """assemble -> (warm) init -> 4 PDIP iterations -> advance, three times; on
+    the 8^3 pile, and on a 6 x 6 x 3 walled box (floor and four side walls)."""
+    s = box_scene(3, n=6, layers=3) if walled else scene_for("pile8", 5)
     sctx = binding.Context()
     dev_s, con = workload.assemble(sctx, s)
     opts = sctx.pdip_opts(sctx.solve_opts(tol=1e-12, maxit=200000))
@@ -94,8 +96,10 @@ def test_three_time_steps_match_oracle(ctx):
     prev = None
     for step in range(3):
         if step > 0:
-            con = sctx.assemble(dev_s, s.floor_z, s.gravity, s.dt, s.delta, s.mu, 3)
+            con = sctx.assemble(dev_s, s.floor_z, s.gravity, s.dt, s.delta, s.mu, 3, s.walls)
         c_o = oc.detect(so)
+        if walled:
+            assert int((c_o.a == so.M).sum()) > 4 * 6 * 3  # wall and floor contacts in every step
         _, N, r = qp.qp_data(so, c_o)
         assert con.Nc == c_o.Nc
         g_d = torch.zeros(con.P, dtype=torch.float64, device="cuda")
@@ -105,13 +109,18 @@ def test_three_time_steps_match_oracle(ctx):
             sctx.pdip_init(st, 1.0)
             g_o, l_o = qp.initial_point(c_o.Nc, so.mu)
         else:
-            sctx.pdip_init_warm(st, prev[0], prev[1], prev[2], 3)
-            g_o, l_o = timestep.warm_start(prev[3], prev[4], prev[5], c_o.a, c_o.b, so.mu)
+            # with walls a sphere can have several contacts with body M: the
+            # plane index keeps them apart on both sides
+            sctx.pdip_init_warm(st, prev[0], prev[1], prev[2], 3, prev_plane=prev[6] if walled else None)
+            g_o, l_o = timestep.warm_start(prev[3], prev[4], prev[5], c_o.a, c_o.b, so.mu,
+                                           prev_plane=prev[7] if walled else None,
+                                           new_plane=c_o.plane if walled else None)
         for _ in range(4):
             sctx.pdip_step(st, opts, allow=())
             g_o, l_o, _ = pdip.pdip_step(N, r, so.mu, g_o, l_o)
         assert_close(qp.from_padded(to_np(g_d), con.Nc, 3), g_o, 1e-6, floor_rel=1e-4, what=f"gamma, step {step}")
-        prev = (workload.view(con, "body_a"), workload.view(con, "body_b"), g_d.clone(), c_o.a, c_o.b, g_o)
+        prev = (workload.view(con, "body_a"), workload.view(con, "body_b"), g_d.clone(), c_o.a, c_o.b, g_o,
+                workload.view(con, "plane"), c_o.plane)
         sctx.advance(st)
         so = timestep.advance(so, c_o, g_o)
     assert_close(soa_to_np(dev_s["vel"]), so.vel, 1e-6, floor_rel=1e-3, what="velocity after three steps")

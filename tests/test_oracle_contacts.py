@@ -103,6 +103,8 @@ def test_wall_contacts_hand_computed():
               walls=walls)
     c = oc.detect(s)
     assert c.Nc == 4 and np.all(c.a == 4)
+    # plane index of each contact: 1 + the wall's position in the list
+    assert sorted(zip(c.b.tolist(), c.plane.tolist())) == [(0, 1), (1, 2), (2, 3), (3, 4)]
     # the midpoint between the sphere surface and the wall
     want = {0: (-0.05, [1, 0, 0], [-1.025, 1.0, 3.0]), 1: (-0.05, [-1, 0, 0], [4.025, 1.0, 3.0]),
             2: (-0.02, [0, 1, 0], [1.5, -0.01, 3.0]), 3: (-0.05, [0, -1, 0], [1.5, 2.525, 3.0])}

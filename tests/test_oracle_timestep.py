@@ -109,3 +109,19 @@ def test_warm_start_identity_on_same_contacts():
         g, lam, _ = pdip.pdip_step(N, r, s.mu, g, lam)
     g2, _ = timestep.warm_start(con.a, con.b, g, con.a, con.b, s.mu, gn0=1e-6, shrink=1.0)
     assert np.array_equal(g2, g)
+
+
+def test_warm_start_keeps_floor_and_wall_apart():
+    """A sphere in contact with the floor and a wall has two contacts (M, b):
+    with plane indices each takes its own previous impulse; without them the
+    two previous impulses cannot both be matched."""
+    prev_a, prev_b = np.array([2, 2]), np.array([0, 0])
+    prev_plane = np.array([0, 1])  # floor, then wall 0
+    prev_gamma = np.array([5.0, 0.1, 0.0, 3.0, 0.0, 0.2])
+    new_a, new_b, new_plane = np.array([2, 2]), np.array([0, 0]), np.array([1, 0])  # order swapped
+    g, lam = timestep.warm_start(prev_a, prev_b, prev_gamma, new_a, new_b, 0.5, gn0=1.0, shrink=0.9,
+                                 prev_plane=prev_plane, new_plane=new_plane)
+    assert np.allclose(g, [3.0, 0.0, 0.2, 5.0, 0.1, 0.0])
+    assert np.all(lam > 0)
+    g2, _ = timestep.warm_start(prev_a, prev_b, prev_gamma, new_a, new_b, 0.5, gn0=1.0, shrink=0.9)
+    assert g2[0] == g2[3]  # one previous contact serves both
