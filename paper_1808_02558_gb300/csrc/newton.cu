@@ -2801,7 +2801,6 @@ static void pdip_pre(qp_ctx* c, qp_state* st, int mode, const qp_pdip_opts* o) {
   coop_launch2(c, k_pdip_pre, grid, A, mode);
 }
 
-// Build (or reuse) the contact partition for a grid of G blocks.
 // Contact partition into G chunks (one per block) with each block's body set.
 static void build_partition(qp_ctx* c, int G, qp::Buf& b_nb, qp::Buf& b_bodies, qp::Buf& b_cl, int& chunk_out,
                             int& maxb_out, int& nbmax_out) {

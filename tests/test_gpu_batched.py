@@ -125,15 +125,17 @@ def test_split_and_unsplit_solves_agree(ctx):
     assert_close(out[2], out[1], 1e-6, floor_rel=1e-2, what="split vs unsplit solve")
 
 
-@pytest.mark.parametrize("tile,cdt", [(0, binding.QP_F32), (1, binding.QP_F32), (2, binding.QP_BF16)])
-def test_batched_qtt_preconditioner(ctx, tile, cdt):
+@pytest.mark.parametrize("tile,cdt,split", [(0, binding.QP_F32, 0), (1, binding.QP_F32, 0), (2, binding.QP_BF16, 0),
+                                            (0, binding.QP_BF16, 1)])
+def test_batched_qtt_preconditioner(ctx, tile, cdt, split):
     """Scenes with their own QTT inverse of their Jacobi-scaled Schur matrix
     (compressed with the state) next to scenes on Jacobi, in one launch.  The
     scenes of up to 2^6 unknowns get exact inverses (ranks up to 64: every rank
     class of the tile table occurs) and take the iteration count of the
     single-scene QTT-PCG with the same inverse; a 2^9 scene gets a truncated one
     (rank 10), which may break down and then finish with Jacobi, as the
-    single-scene solver does.  All: residual 1e-10 against the oracle S."""
+    single-scene solver does.  All: residual 1e-10 against the oracle S.  split
+    0 puts these few scenes on two-block clusters, split 1 on one block each."""
     sc = [lattice_scene(2, 12, mu=0.4), sphere_on_plane((0.3, 0.1, -0.2)), lattice_scene(2, 21, mu=0.7),
           lattice_scene(4, 14, mu=0.6), lattice_scene(3, 40, mu=0.8)]
     rank = [64, 64, 64, 10, None]
@@ -158,8 +160,8 @@ def test_batched_qtt_preconditioner(ctx, tile, cdt):
         S_tt.free()
     assert X[0].d == 6 and X[1].d == 2
     stats, used = binding.newton_solve_batched([p[0].ctx for p in pbs], states, rhs, dx, tol=1e-10, maxit=20000,
-                                               block_threads=256, allow=(), precond=X, core_dtype=cdt,
-                                               qtt_tile=tile)
+                                               block_threads=256, split=split, allow=(), precond=X,
+                                               core_dtype=cdt, qtt_tile=tile)
     for (pb, g, lam), st, r, x, s, Xi, rk in zip(pbs, states, rhs, dx, stats, X, rank):
         assert s.status == binding.QP_OK
         S = qp.schur_matrix(pb.N, g, lam, pb.scene.mu)
