@@ -309,6 +309,77 @@ __global__ void k_gram_partial(long long rows, int n, const double* __restrict__
   }
 }
 
+// The same partial Gram matrices for n = 4 r <= 64, register-tiled: the block
+// stages GR_ROWS rows of its chunk in shared memory, thread t owns the 4 x 4
+// tile (tx, ty), tx <= ty, of the upper triangle in row group g (groups take
+// every G-th staged row, so all 256 threads work at small n); the groups' tiles
+// are then added in group order into the block's partial (both triangles).
+// Partials are summed in block order by k_gram_reduce: the result does not
+// depend on scheduling.  Dynamic shared memory: GR_SMEM bytes.
+constexpr int GR_ROWS = 64;
+constexpr int GR_SMEM = 60 * 1024;  // >= GR_ROWS * 64 doubles and >= G n^2 doubles for every n = 4 r <= 64
+__global__ void __launch_bounds__(256) k_gram_tiled(long long rows, int n, const double* __restrict__ Mx,
+                                                    double* __restrict__ part, long long chunk) {
+  extern __shared__ double gr_sm[];
+  const int T = n >> 2, ntiles = T * (T + 1) / 2;
+  const int G = 256 / ntiles;  // row groups (>= 1 for n <= 64)
+  const int tid = threadIdx.x, g = tid / ntiles, tile = tid - g * ntiles;
+  const bool active = g < G;
+  int tx = 0, ty = 0;
+  if (active) {
+    int rem = tile;
+    while (rem > ty) {
+      rem -= ty + 1;
+      ++ty;
+    }
+    tx = rem;  // 0 <= tx <= ty
+  }
+  double acc[4][4] = {};
+  const long long r0 = blockIdx.x * chunk;
+  const long long r1 = min(rows, r0 + chunk);
+  for (long long base = r0; base < r1; base += GR_ROWS) {
+    const int nr = (int)min((long long)GR_ROWS, r1 - base);
+    __syncthreads();
+    for (int i = tid; i < nr * n; i += 256) gr_sm[i] = Mx[base * n + i];
+    __syncthreads();
+    if (active) {
+      for (int rr = g; rr < nr; rr += G) {
+        const double* row = gr_sm + rr * n;
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a[i] = row[4 * tx + i];
+          b[i] = row[4 * ty + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+  }
+  __syncthreads();
+  const int nn = n * n;
+  if (active) {
+    double* red = gr_sm + g * nn;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int x = 4 * tx + i, y = 4 * ty + j;
+        red[x * n + y] = acc[i][j];
+        red[y * n + x] = acc[i][j];
+      }
+  }
+  __syncthreads();
+  double* out = part + (long long)blockIdx.x * nn;
+  for (int xy = tid; xy < nn; xy += 256) {
+    double v = 0.0;
+    for (int q = 0; q < G; ++q) v += gr_sm[q * nn + xy];
+    out[xy] = v;
+  }
+}
+
 __global__ void k_gram_reduce(int nparts, int n, const double* __restrict__ part, double* __restrict__ G) {
   for (int xy = blockIdx.x * blockDim.x + threadIdx.x; xy < n * n; xy += gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -703,13 +774,22 @@ qp_qtt* compress_impl(qp_ctx* c, bool with_H, double eps, int rmax, const double
     double* Mx = static_cast<double*>(b_M.ensure((size_t)npar * n * sizeof(double)));
     QP_CUDA(cudaMemsetAsync(Mx, 0, (size_t)npar * n * sizeof(double), st));
     k_scatter_rows<<<c->num_sms * 8, 256, 0, st>>>(rows, r, K, pid, W, Mx, Kalt);
-    // Gram
-    const int nparts = (int)std::min<long long>(256, std::max<long long>(1, npar / 64));
-    const long long chunk = (npar + nparts - 1) / nparts;
-    double* gp = static_cast<double*>(b_part.ensure((size_t)nparts * n * n * sizeof(double)));
-    k_gram_partial<<<nparts, 256, 0, st>>>(npar, n, Mx, gp, chunk);
+    // Gram: register-tiled partials for n <= 64, one entry per thread above
     double* G = static_cast<double*>(w.A.ensure((size_t)n * n * sizeof(double)));
-    k_gram_reduce<<<ceil_div((long long)n * n, 256), 256, 0, st>>>(nparts, n, gp, G);
+    if (n <= 64) {
+      const int nparts = (int)std::min<long long>(2 * c->num_sms, std::max<long long>(1, npar / 256));
+      const long long chunk = (npar + nparts - 1) / nparts;
+      double* gp = static_cast<double*>(b_part.ensure((size_t)nparts * n * n * sizeof(double)));
+      QP_CUDA(cudaFuncSetAttribute(k_gram_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
+      k_gram_tiled<<<nparts, 256, GR_SMEM, st>>>(npar, n, Mx, gp, chunk);
+      k_gram_reduce<<<ceil_div((long long)n * n, 256), 256, 0, st>>>(nparts, n, gp, G);
+    } else {
+      const int nparts = (int)std::min<long long>(256, std::max<long long>(1, npar / 64));
+      const long long chunk = (npar + nparts - 1) / nparts;
+      double* gp = static_cast<double*>(b_part.ensure((size_t)nparts * n * n * sizeof(double)));
+      k_gram_partial<<<nparts, 256, 0, st>>>(npar, n, Mx, gp, chunk);
+      k_gram_reduce<<<ceil_div((long long)n * n, 256), 256, 0, st>>>(nparts, n, gp, G);
+    }
     EigArgs ea;
     ea.A = G;
     ea.V = static_cast<double*>(w.V.ensure((size_t)n * n * sizeof(double)));
