@@ -416,7 +416,10 @@ int qtt_set_tensor_cores(qp_ctx_t ctx, int mode);
 /* TT rounding: right-to-left QR orthogonalisation then left-to-right
  * truncated SVD in FP64, keeping per split the smallest rank with discarded
  * norm <= eps ||A||_F / sqrt(d-1), capped at rmax (Sec. 3.1 truncation rule,
- * Alg. 1 accuracy split).                                                   */
+ * Alg. 1 accuracy split).  For eps >= 1e-7 the factorisations go through Gram
+ * matrices (singular values resolved down to about 1e-8 of the largest); for
+ * eps < 1e-7 through one-sided Jacobi on the cores themselves (resolved down
+ * to FP64 rounding), slower at large ranks.                                 */
 int qtt_round(qp_ctx_t ctx, qtt_t A, double eps, int rmax, qtt_t* out);
 
 /* QTT compression of S (st != NULL) or of N (st == NULL) in the padded layout:
@@ -424,7 +427,8 @@ int qtt_round(qp_ctx_t ctx, qtt_t A, double eps, int rmax, qtt_t* out);
  * over the nonzero block rows of each level, same truncation rule as above.
  * Ranks are capped at min(rmax, 128).  The SVDs go through FP64 Gram matrices,
  * which resolve singular values down to about 1e-8 of the largest one, so eps
- * below about 1e-7 does not reduce the error further (same for qtt_round).  */
+ * below about 1e-7 does not reduce the error further (qtt_round does not have
+ * this limit).                                                              */
 int qtt_compress(qp_ctx_t ctx, const qp_state* st, double eps, int rmax, qtt_t* out);
 
 /* Approximate inverse X ~ S^-1 of a QTT matrix by alternating linear-scheme

@@ -152,6 +152,85 @@ __device__ inline void syev(double* A, double* V, double* Vs, double* w, int n, 
   __syncthreads();
 }
 
+// One-sided (Hestenes) Jacobi: the k vectors of length L, element e of vector
+// i at X[i sv + e se], are made mutually orthogonal by plane rotations applied
+// to the vectors themselves (no Gram matrix, so singular values down to FP64
+// rounding of the largest are resolved; Demmel and Veselic, SIAM J. Matrix
+// Anal. Appl. 13 (1992)).  Vr (k x k, row-major) accumulates the rotations:
+// with the vectors as columns, X_new = X_old Vr.  A warp handles one pair of a
+// round-robin round; sweeps stop when no pair had |x_p.x_q| above
+// sqrt(L) eps sqrt(|x_p|^2 |x_q|^2).
+__device__ inline void osj(double* X, int k, int L, long long sv, long long se, double* Vr) {
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int i = tid; i < k * k; i += nt) Vr[i] = (i / k == i % k) ? 1.0 : 0.0;
+  const double tol = sqrt((double)L) * 2.2e-16;
+  const int m = k + (k & 1), npairs = m / 2;
+  __syncthreads();
+  for (int sweep = 0; sweep < 60 && k > 1; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r) {
+      for (int i = warp; i < npairs; i += nw) {
+        int p, q;
+        rr_pair(m, r, i, p, q);
+        if (q >= k) continue;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int e = lane; e < L; e += 32) {
+          const double xp = X[p * sv + e * se], xq = X[q * sv + e * se];
+          al += xp * xp;
+          be += xq * xq;
+          ga += xp * xq;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (fabs(ga) > 1e-300 && fabs(ga) > tol * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+          for (int e = lane; e < L; e += 32) {
+            const double xp = X[p * sv + e * se], xq = X[q * sv + e * se];
+            X[p * sv + e * se] = c * xp - sn * xq;
+            X[q * sv + e * se] = sn * xp + c * xq;
+          }
+          for (int j = lane; j < k; j += 32) {
+            const double vp = Vr[j * k + p], vq = Vr[j * k + q];
+            Vr[j * k + p] = c * vp - sn * vq;
+            Vr[j * k + q] = sn * vp + c * vq;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+}
+
+// Norms of the k vectors of X (as in osj) into sig, and ord[j] = the index of
+// the j-th largest (ties by index).
+__device__ inline void osj_norms(const double* X, int k, int L, long long sv, long long se, double* sig, int* ord) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < k; i += nt) {
+    double s = 0.0;
+    for (int e = 0; e < L; ++e) s += X[i * sv + e * se] * X[i * sv + e * se];
+    sig[i] = sqrt(s);
+  }
+  __syncthreads();
+  for (int i = tid; i < k; i += nt) {
+    int rank = 0;
+    for (int j = 0; j < k; ++j)
+      if (sig[j] > sig[i] || (sig[j] == sig[i] && j < i)) ++rank;
+    ord[rank] = i;
+  }
+  __syncthreads();
+}
+
 // Smallest r with sqrt(sum_{l >= r} lambda_l) <= delta, 1 <= r <= min(rmax, n)
 // (eigenvalues of a Gram matrix, descending: the squared singular values).
 __device__ inline int trunc_rank(const double* lam, int n, double delta, int rmax) {

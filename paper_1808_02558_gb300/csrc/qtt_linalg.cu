@@ -51,16 +51,56 @@ struct RoundArgs {
   double* norm_out;
 };
 
+// Below eps = 1e-7 the SVDs are one-sided Jacobi on the cores themselves (the
+// Gram route resolves singular values only down to about 1e-8 sigma_max);
+// above, the Gram matrices and the shared eigensolver, which are faster at
+// large ranks on the narrow FP64 pipe.
 __global__ void __launch_bounds__(LT) k_tt_round(RoundArgs a) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int d = a.d;
   __shared__ int sh_r;
+  const bool accurate = a.eps < 1e-7;
+  int* ord = reinterpret_cast<int*>(a.A);  // order of the singular values (accurate path)
   // right-to-left orthogonalisation: core_k = R Q with orthonormal rows of Q
   for (int k = d - 1; k >= 1; --k) {
     const int rk = a.ranks[k], rn = a.ranks[k + 1], rp = a.ranks[k - 1];
     double* B = a.cores + (long long)k * a.cap;         // rk x 4rn
     double* Cp = a.cores + (long long)(k - 1) * a.cap;  // (rp*4) x rk
     const int nc = 4 * rn;
+    if (accurate) {
+      // rows of B made orthogonal: B = Vr (Sigma Q); Q's rows are the normalised
+      // rows, Vr Sigma moves into core_{k-1}; rows at FP64 rounding are dropped
+      dla::osj(B, rk, nc, nc, 1, a.V);
+      dla::osj_norms(B, rk, nc, nc, 1, a.w, ord);
+      if (tid == 0) {
+        const double smax = a.w[ord[0]];
+        int r = 0;
+        while (r < rk && a.w[ord[r]] > 1e-15 * smax && a.w[ord[r]] > 0.0) ++r;
+        sh_r = r < 1 ? 1 : r;
+      }
+      __syncthreads();
+      const int r = sh_r;
+      for (int i = tid; i < r * nc; i += nt) {
+        const int x = i / nc, cc = i - x * nc;
+        const double sg = a.w[ord[x]];
+        a.tmp[i] = sg > 0.0 ? B[ord[x] * nc + cc] / sg : 0.0;
+      }
+      __syncthreads();
+      for (int i = tid; i < r * nc; i += nt) B[i] = a.tmp[i];
+      __syncthreads();
+      const int mrow = rp * 4;
+      for (int i = tid; i < mrow * r; i += nt) {
+        const int x = i / r, y = i - x * r;
+        double sm = 0.0;
+        for (int z = 0; z < rk; ++z) sm += Cp[x * rk + z] * a.V[z * rk + ord[y]];
+        a.tmp[i] = sm * a.w[ord[y]];
+      }
+      __syncthreads();
+      for (int i = tid; i < mrow * r; i += nt) Cp[i] = a.tmp[i];
+      if (tid == 0) a.ranks[k] = r;
+      __syncthreads();
+      continue;
+    }
     for (int i = tid; i < rk * rk; i += nt) {
       int x = i / rk, y = i - x * rk;
       double s = 0.0;
@@ -116,6 +156,37 @@ __global__ void __launch_bounds__(LT) k_tt_round(RoundArgs a) {
     double* C = a.cores + (long long)k * a.cap;            // (rk*4) x rn
     double* Cn = a.cores + (long long)(k + 1) * a.cap;     // rn x 4 r2
     const int mrow = rk * 4;
+    if (accurate) {
+      // columns of C made orthogonal: C = (U Sigma) Vr^T; core_k <- U[:, :r],
+      // core_{k+1} <- Sigma Vr[:, :r]^T core_{k+1}, r by the truncation rule on sigma^2
+      dla::osj(C, rn, mrow, 1, rn, a.V);
+      dla::osj_norms(C, rn, mrow, 1, rn, a.Vs, ord);
+      for (int i = tid; i < rn; i += nt) a.w[i] = a.Vs[ord[i]] * a.Vs[ord[i]];
+      __syncthreads();
+      if (tid == 0) sh_r = trunc_rank(a.w, rn, delta, a.rmax);
+      __syncthreads();
+      const int r = sh_r;
+      for (int i = tid; i < mrow * r; i += nt) {
+        const int x = i / r, y = i - x * r;
+        const double sg = a.Vs[ord[y]];
+        a.tmp[i] = sg > 0.0 ? C[x * rn + ord[y]] / sg : 0.0;
+      }
+      __syncthreads();
+      for (int i = tid; i < mrow * r; i += nt) C[i] = a.tmp[i];
+      __syncthreads();
+      const int nc = 4 * r2;
+      for (int i = tid; i < r * nc; i += nt) {
+        const int x = i / nc, cc = i - x * nc;
+        double sm = 0.0;
+        for (int z = 0; z < rn; ++z) sm += a.V[z * rn + ord[x]] * Cn[z * nc + cc];
+        a.tmp[i] = sm * a.Vs[ord[x]];
+      }
+      __syncthreads();
+      for (int i = tid; i < r * nc; i += nt) Cn[i] = a.tmp[i];
+      if (tid == 0) a.ranks[k + 1] = r;
+      __syncthreads();
+      continue;
+    }
     for (int i = tid; i < rn * rn; i += nt) {
       int x = i / rn, y = i - x * rn;
       double s = 0.0;

@@ -173,15 +173,19 @@ def test_round_sum_recovers_ranks(ctx):
     cores = tt.qtt_compress_dense(A, 1e-3)
     dbl = tt.tt_add(cores, cores)
     G = ctx.qtt_from_cores(dbl)
-    # the one-block FP64 SVD works on Gram matrices: singular values below about
-    # 1e-8 sigma_max are not resolved, so exact rank recovery is checked at eps = 1e-6
-    R = ctx.qtt_round(G, 1e-6)
-    assert R.ranks() == tt.tt_ranks(cores)
+    # below eps = 1e-7 the SVDs are one-sided Jacobi on the cores (no Gram
+    # matrix): the redundant half of the doubled ranks sits at FP64 rounding and
+    # is removed even at eps = 1e-12; at eps = 1e-6 the Gram route does it
     want = 2 * tt.qtt_matrix(cores)
-    assert_close(tt.qtt_matrix(R.cores()), want, 1e-5, floor_rel=1e-2, what="round(A + A)")
+    for eps in (1e-12, 1e-6):
+        R = ctx.qtt_round(G, eps)
+        assert R.ranks() == tt.tt_ranks(cores), (eps, R.ranks(), tt.tt_ranks(cores))
+        assert_close(tt.qtt_matrix(R.cores()), want, 1e-9 if eps < 1e-7 else 1e-5, floor_rel=1e-2,
+                     what=f"round(A + A), eps {eps}")
 
 
-@pytest.mark.parametrize("eps,rmax", [(1e-1, 1000), (1e-2, 1000), (1e-2, 6), (1e-6, 1000)])
+@pytest.mark.parametrize("eps,rmax", [(1e-1, 1000), (1e-2, 1000), (1e-2, 6), (1e-6, 1000), (1e-10, 1000),
+                                      (1e-12, 7)])
 def test_round_matches_oracle(ctx, eps, rmax):
     rng = np.random.default_rng(11)
     d = 8
