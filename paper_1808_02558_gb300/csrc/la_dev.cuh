@@ -94,30 +94,37 @@ __device__ inline void jacobi_sweeps(double* A, double* V, int n) {
         rs[i] = s;
       }
       __syncthreads();
-      // rows p, q  <-  J^T A
-      for (int idx = tid; idx < npairs * n; idx += nt) {
-        const int i = idx / n, j = idx - i * n;
-        const int p = rp[i], q = rq[i];
-        if (q >= n || rs[i] == 0.0) continue;
-        const double c = rc[i], s = rs[i];
-        const double a = A[p * n + j], b = A[q * n + j];
-        A[p * n + j] = c * a - s * b;
-        A[q * n + j] = s * a + c * b;
-      }
-      __syncthreads();
-      // columns p, q  <-  A J  and  V J
-      for (int idx = tid; idx < npairs * n; idx += nt) {
-        const int i = idx / n, j = idx - i * n;
-        const int p = rp[i], q = rq[i];
-        if (q >= n || rs[i] == 0.0) continue;
-        const double c = rc[i], s = rs[i];
-        double a = A[j * n + p], b = A[j * n + q];
-        A[j * n + p] = c * a - s * b;
-        A[j * n + q] = s * a + c * b;
-        a = V[j * n + p];
-        b = V[j * n + q];
-        V[j * n + p] = c * a - s * b;
-        V[j * n + q] = s * a + c * b;
+      // A <- J^T A J in one pass: J is block diagonal in the pairs, so the 2 x 2
+      // block of rows (p_i, q_i) and columns (p_j, q_j) becomes J_i^T A_ij J_j;
+      // one thread per block (a missing q of the odd pair is left out), and
+      // V <- V J for one row and pair per thread
+      const int nblk = npairs * npairs;
+      for (int idx = tid; idx < nblk + npairs * n; idx += nt) {
+        if (idx < nblk) {
+          const int i = idx / npairs, j = idx - i * npairs;
+          const int p = rp[i], q = rq[i], p2 = rp[j], q2 = rq[j];
+          const double ci = rc[i], si = rs[i], cj = rc[j], sj = rs[j];
+          if (si == 0.0 && sj == 0.0) continue;
+          const bool hq = q < n, hq2 = q2 < n;
+          const double a00 = A[p * n + p2], a01 = hq2 ? A[p * n + q2] : 0.0;
+          const double a10 = hq ? A[q * n + p2] : 0.0, a11 = (hq && hq2) ? A[q * n + q2] : 0.0;
+          // rows: (J_i^T A): row p <- c a_p - s a_q, row q <- s a_p + c a_q
+          const double b00 = ci * a00 - si * a10, b01 = ci * a01 - si * a11;
+          const double b10 = si * a00 + ci * a10, b11 = si * a01 + ci * a11;
+          // columns: (. J_j): col p2 <- c b_p2 - s b_q2, col q2 <- s b_p2 + c b_q2
+          A[p * n + p2] = cj * b00 - sj * b01;
+          if (hq2) A[p * n + q2] = sj * b00 + cj * b01;
+          if (hq) A[q * n + p2] = cj * b10 - sj * b11;
+          if (hq && hq2) A[q * n + q2] = sj * b10 + cj * b11;
+        } else {
+          const int u = idx - nblk, i = u / n, j = u - i * n;
+          const int p = rp[i], q = rq[i];
+          if (q >= n || rs[i] == 0.0) continue;
+          const double c = rc[i], s = rs[i];
+          const double a = V[j * n + p], b = V[j * n + q];
+          V[j * n + p] = c * a - s * b;
+          V[j * n + q] = s * a + c * b;
+        }
       }
       __syncthreads();
     }
