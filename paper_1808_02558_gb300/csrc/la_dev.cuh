@@ -50,12 +50,50 @@ __device__ __forceinline__ void rr_pair(int m, int r, int i, int& p, int& q) {
   }
 }
 
+// Rotation (c, s) annihilating a_pq of the 2 x 2 block [[a_pp, a_pq], [a_pq,
+// a_qq]] (a_pq != 0).  precise: the angle in FP64.  Otherwise the angle comes
+// from FP32 arithmetic on the block scaled by a power of two (FP64 division and
+// square root are long dependent sequences on GB300's narrow FP64 pipe), and
+// (c, s) is made a rotation to FP64 rounding by two Newton steps towards
+// c^2 + s^2 = 1: the rotation stays exactly orthogonal and only its angle
+// carries the FP32 error, which the next sweep removes (the sweeps switch to
+// precise angles once the off-diagonal part is small).
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, bool precise, double& c,
+                                                double& s) {
+  if (!precise) {
+    const double num = aqq - app, den = 2.0 * apq;
+    int e;
+    frexp(fmax(fabs(num), fabs(den)), &e);
+    const float nf = (float)ldexp(num, -e), df = (float)ldexp(den, -e);
+    if (df != 0.0f && isfinite(nf / df)) {
+      const float tau = nf / df;
+      // large |tau|: t = 1 / (2 tau) to FP32 rounding (tau^2 would overflow)
+      const float t = fabsf(tau) > 1e18f ? 0.5f / tau
+                                         : (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+      const float cf = rsqrtf(1.0f + t * t);
+      double cc = (double)cf, ss = (double)(t * cf);
+      for (int it = 0; it < 2; ++it) {
+        const double f = 1.5 - 0.5 * (cc * cc + ss * ss);
+        cc *= f;
+        ss *= f;
+      }
+      c = cc;
+      s = ss;
+      return;
+    }
+  }
+  const double tau = (aqq - app) / (2.0 * apq);
+  const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
 // Jacobi sweeps on A (n x n, row-major, destroyed); V accumulates the
 // rotations (starts as I).  A and V may live in shared or global memory.
 __device__ inline void jacobi_sweeps(double* A, double* V, int n) {
   __shared__ double rc[256], rs[256];
   __shared__ int rp[256], rq[256];
-  __shared__ int done;
+  __shared__ int done, precise;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
   __syncthreads();
@@ -70,9 +108,13 @@ __device__ inline void jacobi_sweeps(double* A, double* V, int n) {
     }
     off = block_sum(off);
     on = block_sum(on);
-    if (tid == 0) done = (off <= 1e-30 * on) || (on == 0.0);
+    if (tid == 0) {
+      done = (off <= 1e-30 * on) || (on == 0.0);
+      precise = off <= 1e-16 * on;  // off-diagonal below 1e-8 of the diagonal: FP64 angles
+    }
     __syncthreads();
     if (done) break;
+    const bool prec = precise != 0;
     for (int r = 0; r < m - 1; ++r) {
       for (int i = tid; i < npairs; i += nt) {
         int p, q;
@@ -81,12 +123,7 @@ __device__ inline void jacobi_sweeps(double* A, double* V, int n) {
         if (q < n) {
           const double apq = A[p * n + q];
           const double app = A[p * n + p], aqq = A[q * n + q];
-          if (apq != 0.0 && fabs(apq) > 1e-300) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
+          if (apq != 0.0 && fabs(apq) > 1e-300) jacobi_rotation(app, aqq, apq, prec, c, s);
         }
         rp[i] = p;
         rq[i] = q;
