@@ -133,12 +133,19 @@ __device__ inline void jacobi_sweeps(double* A, double* V, int n) {
       __syncthreads();
       // A <- J^T A J in one pass: J is block diagonal in the pairs, so the 2 x 2
       // block of rows (p_i, q_i) and columns (p_j, q_j) becomes J_i^T A_ij J_j;
-      // one thread per block (a missing q of the odd pair is left out), and
-      // V <- V J for one row and pair per thread
-      const int nblk = npairs * npairs;
+      // A stays symmetric, so a thread forms block (i, j), i <= j, and writes its
+      // transpose into block (j, i) as well (a missing q of the odd pair is left
+      // out); V <- V J for one row and pair per thread
+      const int nblk = npairs * (npairs + 1) / 2;
       for (int idx = tid; idx < nblk + npairs * n; idx += nt) {
         if (idx < nblk) {
-          const int i = idx / npairs, j = idx - i * npairs;
+          // block index -> (i, j), i <= j: row i holds npairs - i blocks
+          int i = 0, rem = idx;
+          while (rem >= npairs - i) {
+            rem -= npairs - i;
+            ++i;
+          }
+          const int j = i + rem;
           const int p = rp[i], q = rq[i], p2 = rp[j], q2 = rq[j];
           const double ci = rc[i], si = rs[i], cj = rc[j], sj = rs[j];
           if (si == 0.0 && sj == 0.0) continue;
@@ -149,10 +156,18 @@ __device__ inline void jacobi_sweeps(double* A, double* V, int n) {
           const double b00 = ci * a00 - si * a10, b01 = ci * a01 - si * a11;
           const double b10 = si * a00 + ci * a10, b11 = si * a01 + ci * a11;
           // columns: (. J_j): col p2 <- c b_p2 - s b_q2, col q2 <- s b_p2 + c b_q2
-          A[p * n + p2] = cj * b00 - sj * b01;
-          if (hq2) A[p * n + q2] = sj * b00 + cj * b01;
-          if (hq) A[q * n + p2] = cj * b10 - sj * b11;
-          if (hq && hq2) A[q * n + q2] = sj * b10 + cj * b11;
+          const double c00 = cj * b00 - sj * b01, c01 = sj * b00 + cj * b01;
+          const double c10 = cj * b10 - sj * b11, c11 = sj * b10 + cj * b11;
+          A[p * n + p2] = c00;
+          if (hq2) A[p * n + q2] = c01;
+          if (hq) A[q * n + p2] = c10;
+          if (hq && hq2) A[q * n + q2] = c11;
+          if (i != j) {  // the mirrored block (j, i)
+            A[p2 * n + p] = c00;
+            if (hq2) A[q2 * n + p] = c01;
+            if (hq) A[p2 * n + q] = c10;
+            if (hq && hq2) A[q2 * n + q] = c11;
+          }
         } else {
           const int u = idx - nblk, i = u / n, j = u - i * n;
           const int p = rp[i], q = rq[i];
